@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the batched 1D C2C FFT (FP32) on the n = 2^8..2^20 sweep.
+
+One step is the whole sweep: for every n = 2^e (e = 8..20, batch = 2^26 / n), both
+complex layouts (interleaved, split) and both directions, one batched transform of
+512 MiB in / 512 MiB out, read from and written to buffers larger than L2.
+Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fftc|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of
+the same workload. Multi-GPU runs (torchrun) are independent replicas of the sweep
+(the transforms of a batch shard with no exchange), reported as weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched C2C FFT GFLOP/s (5n·log2n) & %HBM roofline, FP32 vs split-FP16"
+UNIT = "GFLOP/s"
+ELEMS = 1 << 26               # n * batch for every sweep size
+SIZES = list(range(8, 21))     # log2 n
+LAYOUTS = ["interleaved", "split"]
+DIRECTIONS = [False, True]     # inverse?
+WORKLOAD = "batched FP32 C2C FFT sweep n=2^8..2^20, n*batch=2^26, interleaved+split, forward+inverse"
+SEED = 2
+
+
+def flops(n: int, batch: int) -> float:
+    return 5.0 * n * math.log2(n) * batch
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+# --------------------------------------------------------------------------
+def oracle_sample(rows_per_size: int):
+    """Time the FP64 oracle (as it stands) on `rows_per_size` rows of every sweep size."""
+    import numpy as np
+
+    import oracle
+    import synthetic_inputs as si
+    threads = oracle.default_threads()
+    oracle.build_oracle()
+    total_flops, total_s = 0.0, 0.0
+    for e in SIZES:
+        n = 1 << e
+        x = si.uniform_complex(rows_per_size, n, seed=SEED * 100 + e).astype(np.complex128)
+        t0 = time.perf_counter()
+        oracle.fft(x, threads=threads)
+        total_s += time.perf_counter() - t0
+        total_flops += flops(n, rows_per_size)
+    return total_flops, total_s, threads
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    import oracle
+    threads = oracle.default_threads()
+    rows = threads
+    for _ in range(args.warmup):
+        oracle_sample(rows)
+    fl, secs = 0.0, 0.0
+    for _ in range(args.steps):
+        f, s, threads = oracle_sample(rows)
+        fl += f
+        secs += s
+    value = fl / secs / 1e9
+    sample = f"{rows} rows of each n=2^8..2^20 (forward) per step; direct O(n^2) DFT for n<=4096, radix-2 above"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the GPU arm
+# --------------------------------------------------------------------------
+def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    import synthetic_inputs as si
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    # one 512 MiB input (viewed at every shape: n * batch is constant) and one output
+    x_host = si.uniform_complex(1, ELEMS, seed=SEED).reshape(ELEMS)
+    x = torch.from_numpy(x_host.view(np.float32)).to(dev)          # 2^27 floats
+    y = torch.empty_like(x)
+    plans = []
+    for e in SIZES:
+        n = 1 << e
+        B = ELEMS // n
+        for layout in LAYOUTS:
+            for inv in DIRECTIONS:
+                plans.append((e, layout, inv, fc.Plan(n, B, layout, inv, device=dev)))
+
+    def views(layout, n, B):
+        if layout == "interleaved":
+            return x.view(torch.complex64).view(B, n), y.view(torch.complex64).view(B, n)
+        return x.view(2, B, n), y.view(2, B, n)
+
+    def step():
+        for e, layout, inv, p in plans:
+            n = 1 << e
+            xi, yo = views(layout, n, ELEMS // n)
+            p.execute(xi, yo)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for *_, p in plans:
+        p.timing(True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    if dist:
+        tm = torch.tensor([ms], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+
+    # per-kernel durations from the library's event probe
+    kinds = {}
+    per_size = []
+    launches = 0
+    for e, layout, inv, p in plans:
+        pm, cnt = p.pass_times()
+        passes, _ = p.info()
+        launches += passes * cnt
+        n = 1 << e
+        names = ["rows"] if passes == 1 else ["cols", "rowst"]
+        for i, nm in enumerate(names):
+            k = kinds.setdefault(nm, {"ms": 0.0, "launches": 0})
+            k["ms"] += pm[i]
+            k["launches"] += cnt
+        t_exec = sum(pm[:passes]) / max(cnt, 1)
+        per_size.append({"n": n, "layout": layout, "dir": "inv" if inv else "fwd", "passes": passes,
+                         "ms": round(t_exec, 4), "gflops": round(flops(n, ELEMS // n) / t_exec / 1e6, 1),
+                         "hbm_frac_strict": round(16.0 * ELEMS / (t_exec * 1e-3) / 1e9 / peaks()[0], 4),
+                         "hbm_frac_per_pass": round(16.0 * ELEMS * passes / (t_exec * 1e-3) / 1e9 / peaks()[0], 4)})
+        p.timing(False)
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    dom_avg_ms = kinds[dom]["ms"] / kinds[dom]["launches"]
+    bytes_per_launch = 16.0 * ELEMS
+    peak, peak_kind = peaks()
+    achieved = bytes_per_launch / (dom_avg_ms * 1e-3) / 1e9
+    step_flops = sum(flops(1 << e, ELEMS // (1 << e)) for e, *_ in plans)
+    value = world * step_flops * args.steps / (ms * 1e-3) / 1e9
+
+    # end to end: host buffers in and out through fftc_execute_host, copies timed
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(x_host.view(np.float32).copy()).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for e, layout, inv, p in plans:
+                p.execute_host(h_in, h_out, y)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        if dist:
+            tm = torch.tensor([wall], device=dev)
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            wall = float(tm.item())
+        e2e = {"value": world * step_flops * args.e2e_steps / wall / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * ELEMS * len(plans), "d2h_bytes_per_step": 8 * ELEMS * len(plans),
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = 0
+        import oracle
+        rows = oracle.default_threads()
+        f, s, th = oracle_sample(rows)
+        cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"{rows} rows of each n=2^8..2^20 (forward, FP64); direct O(n^2) DFT for n<=4096, "
+                         f"radix-2 above; {s:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": "2^8..2^20", "n_times_batch": ELEMS,
+                       "layouts": LAYOUTS, "directions": ["forward", "inverse"],
+                       "l2": "no flush: every buffer is 512 MiB, larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                         "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": None, "bytes_per_launch": bytes_per_launch,
+                         "avg_launch_ms": round(dom_avg_ms, 5), "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()}},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "per_size": per_size,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fftc", "reference"], default="fftc")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_fftc(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

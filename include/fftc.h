@@ -1,0 +1,168 @@
+/*
+ * fftc.h -- C ABI of the GB300 batched 1D complex-to-complex FFT library (libfftc.so).
+ *
+ * The library computes, for every row of a batch,
+ *     X_k = sum_{j<n} x_j * exp(s * 2*pi*i * j*k / n),   k = 0..n-1,
+ * with s = -1 (FFTC_FORWARD) or s = +1 (FFTC_INVERSE) and no normalisation in
+ * either direction, so inverse(forward(x)) = n * x. The arithmetic follows the
+ * Cooley-Tukey factorisation of the paper's Eq. 1 (Section 3),
+ *     DFT_N = (DFT_K (x) I_M) . D^N_M . (I_K (x) DFT_M) . Pi^N_K ,   N = M*K,
+ * applied recursively inside fused Stockham kernels (Section 4 benchmarks the
+ * Stockham form), over the two complex layouts of Section 3, step 3
+ * ("Interleaved" and "Split").
+ *
+ * Conventions shared by every call:
+ *   - All data pointers passed to fftc_execute are DEVICE pointers on the
+ *     device that was current when the plan was created, 16-byte aligned.
+ *   - A plan owns its device memory (twiddle tables, workspace, descriptor
+ *     tables); fftc_execute never allocates, never synchronises the host and
+ *     only enqueues work on the given stream.
+ *   - A plan must not be executed concurrently on two streams (it may own a
+ *     workspace). Distinct plans are independent.
+ *   - Errors are reported only through the returned status; nothing aborts,
+ *     throws or exits.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ */
+#ifndef FFTC_H
+#define FFTC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftc_plan_s *fftc_plan; /* opaque, owned by the library */
+
+/* Complex layouts (Section 3, step 3).
+ * INTERLEAVED: one buffer [batch][n] of (float re, float im) pairs (complex64).
+ * SPLIT:       one buffer holding two planes, re[batch][n] then im[batch][n]
+ *              (a float32 array of shape [2, batch, n]). */
+typedef enum { FFTC_LAYOUT_INTERLEAVED = 0, FFTC_LAYOUT_SPLIT = 1 } fftc_layout;
+
+/* Sign of the exponent. */
+typedef enum { FFTC_FORWARD = -1, FFTC_INVERSE = +1 } fftc_direction;
+
+/* Arithmetic of the radix stages.
+ * FP32:           every stage in float32 on CUDA cores.
+ * *_TC:           radix-16 stages as dense 16x16 complex DFT-matrix products on the
+ *                 tensor cores with FP16 or BF16 operands and FP32 accumulation.
+ * *_TC_SPLIT:     as *_TC, but each operand is split into hi + lo parts and the three
+ *                 products hi*hi + hi*lo + lo*hi are accumulated, recovering most of
+ *                 the FP32 accuracy. */
+typedef enum {
+    FFTC_FP32 = 0,
+    FFTC_FP16_TC = 1,
+    FFTC_BF16_TC = 2,
+    FFTC_FP16_TC_SPLIT = 3,
+    FFTC_BF16_TC_SPLIT = 4
+} fftc_precision;
+
+typedef enum {
+    FFTC_OK = 0,
+    FFTC_ERR_INVALID_VALUE = 1,   /* a NULL pointer, a bad enum, a negative count */
+    FFTC_ERR_UNSUPPORTED_SIZE = 2,/* n not a power of two in [2, 2^20], or batch too large */
+    FFTC_ERR_MISALIGNED = 3,      /* a data pointer not 16-byte aligned */
+    FFTC_ERR_ALLOC = 4,           /* device or host allocation failed in plan creation */
+    FFTC_ERR_CUDA = 5,            /* a CUDA runtime call or kernel launch failed */
+    FFTC_ERR_INVALID_PLAN = 6,    /* NULL where a plan is required, or a destroyed plan */
+    FFTC_ERR_TIMEOUT = 7          /* a bounded device-side wait gave up (see fftc_plan_check) */
+} fftc_status;
+
+/*
+ * Create a plan for `batch` transforms of length n (n = 2^e, 2 <= n <= 2^20), in
+ * the given layout, direction and precision, on the current CUDA device.
+ * Precomputes the twiddle diagonals D (Eq. 1; Table 1 "Mul") in FP64 with exact
+ * integer angle reduction and rounds them once to the working precision.
+ * Returns NULL on error; fftc_get_last_error() then tells why.
+ * Tensor-core precisions require n >= 16.
+ */
+fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_direction direction,
+                           fftc_precision precision);
+
+/*
+ * Enqueue the plan's transforms on `stream`: read `in`, write `out` (device pointers,
+ * 16-byte aligned, each n*batch complex elements in the plan's layout). in == out
+ * (in place) is allowed; otherwise the buffers must not overlap. For an uneven plan
+ * the buffers hold the rows back to back at the plan's offsets.
+ * Returns FFTC_OK once the work is enqueued (kernel faults surface on the stream).
+ */
+fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream);
+
+/*
+ * Same transforms, with HOST buffers: copies `host_in` to `dev_buf` (a caller-owned
+ * device buffer of at least fftc_plan_bytes() bytes), transforms it in place, copies
+ * the result to `host_out`, and waits for the stream. Host buffers should be pinned
+ * (page-locked) for the copies to run at full speed. Meant for end-to-end timing.
+ */
+fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_out, void *dev_buf,
+                              void *stream);
+
+/*
+ * out[b][k] = scale * h[k] * X_b[k]: the plan's transforms with a real factor per output
+ * frequency fused into the last pass (the diagonal step of a spectral filter, whose
+ * adjoint is the same call on the opposite-direction plan). `h` is a device array of n
+ * floats (16-byte aligned); the rest is as in fftc_execute. FFTC_FP32 plans only.
+ */
+fftc_status fftc_execute_pointwise(fftc_plan plan, const void *in, void *out, const float *h, float scale,
+                                   void *stream);
+
+/* Bytes of one input (or output) buffer of the plan; 0 for an invalid plan. */
+int64_t fftc_plan_bytes(fftc_plan plan);
+
+/* Release the plan and its device memory. NULL is a no-op returning FFTC_OK. */
+fftc_status fftc_destroy(fftc_plan plan);
+
+/* Status of the last fftc_plan_create* call on this host thread. */
+fftc_status fftc_get_last_error(void);
+
+/* Static, human-readable name of a status code. */
+const char *fftc_status_string(fftc_status s);
+
+/*
+ * Describe the plan's factorisation: the number of HBM passes (1, or 2 for the
+ * four-step split n = M*K of Eq. 1 applied once at the memory level) and the radix
+ * of every stage in execution order (at most 16 entries). Any output pointer may
+ * be NULL. For an uneven plan, passes = 1 and the radices are those of its longest row.
+ */
+fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices);
+
+/*
+ * Uneven batch: `count` transforms, row i of length n[i] (a power of two, 64..2^16)
+ * with direction[i] in {-1, +1}, stored back to back at complex-element offset
+ * offset[i] in the input and output buffers (rows must not overlap). One execute is
+ * one persistent-kernel launch, replayed from a CUDA graph captured at the first
+ * execute on a given (in, out, stream). n, direction and offset are host arrays,
+ * copied into the plan. Only FFTC_FP32 is supported here.
+ */
+fftc_plan fftc_plan_create_uneven(int64_t count, const int64_t *n, const int8_t *direction,
+                                  const int64_t *offset, fftc_layout layout,
+                                  fftc_precision precision);
+
+/*
+ * Read and clear the plan's device error word after its work has finished (this call
+ * synchronises `stream`). Returns FFTC_ERR_TIMEOUT if a bounded device-side wait of
+ * the plan gave up since the last check, FFTC_OK otherwise.
+ */
+fftc_status fftc_plan_check(fftc_plan plan, void *stream);
+
+/*
+ * Timing probe for benchmarks. With enable != 0 every later execute of the plan records
+ * a CUDA event on its stream before the first pass, between passes and after the last
+ * pass (at most 4096 executes are kept; later ones are not recorded). With enable == 0
+ * the probe stops and its records are dropped. Events are created here, not in execute.
+ */
+fftc_status fftc_plan_timing(fftc_plan plan, int enable);
+
+/*
+ * Per-pass device time of the executes recorded since the probe was enabled:
+ * ms_per_pass[i] = summed elapsed milliseconds of pass i (i < 2), *executes = how many
+ * executes were recorded. Synchronises on the recorded events.
+ */
+fftc_status fftc_plan_pass_times(fftc_plan plan, double *ms_per_pass, int *executes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTC_H */

@@ -1,0 +1,329 @@
+// C ABI of libfftc.so: plan creation (radix/pass planning, FP64 twiddle tables,
+// workspace), execution and error reporting. See include/fftc.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "../../include/fftc.h"
+#include "fftc_internal.h"
+#include "fftc_plan.h"
+
+using namespace fftc;
+
+namespace fftc {
+
+// ---------------------------------------------------------------------------
+// schedule mirror and registry
+// ---------------------------------------------------------------------------
+HostSched host_sched(int logl, int loge) {
+    HostSched h{};
+    if (loge > logl) loge = logl;
+    h.S = (logl + loge - 1) / loge;
+    const int rem = logl % loge;
+    int acc = 0;
+    for (int s = 0; s < h.S; ++s) {
+        h.lr[s] = (s == 0 && rem) ? rem : loge;
+        h.lns[s] = acc;
+        acc += h.lr[s];
+    }
+    int o = 0;
+    for (int s = 1; s < h.S; ++s) o += ((1 << h.lr[s]) - 1) << h.lns[s];
+    h.tw_total = o;
+    return h;
+}
+
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout) {
+    for (int i = 0; i < kernel_count(); ++i) {
+        const KernelEntry *e = kernel_at(i);
+        if (e->kind == kind && e->logl == logl && e->loge == loge && e->lines == lines && e->lin == lin &&
+            e->lout == lout)
+            return e;
+    }
+    return nullptr;
+}
+
+// cos and sin of 2*pi*m/L in FP64 with exact integer reduction of the angle to
+// the first octant (the fraction m/L is kept as an exact ratio of integers).
+void unit_root(int64_t m, int64_t L, double *cosv, double *sinv) {
+    m %= L;
+    if (m < 0) m += L;
+    int64_t num = m, den = L;
+    double sc = 1.0, ss = 1.0;
+    bool swap = false;
+    if (2 * num >= den) {  // f >= 1/2: f - 1/2, both parts negate
+        num = 2 * num - den;
+        den *= 2;
+        sc = -sc;
+        ss = -ss;
+    }
+    if (4 * num > den) {  // f > 1/4: 1/2 - f, cosine negates
+        num = den - 2 * num;
+        den *= 2;
+        sc = -sc;
+    }
+    if (8 * num > den) {  // f > 1/8: 1/4 - f, cosine and sine swap
+        num = den - 4 * num;
+        den *= 4;
+        swap = true;
+    }
+    const double th = 6.283185307179586476925286766559 * ((double)num / (double)den);
+    double c = std::cos(th), s = std::sin(th);
+    if (swap) {
+        double t = c;
+        c = s;
+        s = t;
+    }
+    *cosv = sc * c;
+    *sinv = ss * s;
+}
+
+// w_L^e = exp(-2 pi i e / L), rounded once to float.
+static float2 omega_f32(int64_t e, int64_t L) {
+    double c, s;
+    unit_root(e, L, &c, &s);
+    return make_float2((float)c, (float)-s);
+}
+
+void stage_twiddles(int logl, int loge, std::vector<float2> &out) {
+    HostSched h = host_sched(logl, loge);
+    out.assign(h.tw_total > 0 ? h.tw_total : 1, make_float2(1.f, 0.f));
+    int off = 0;
+    for (int s = 1; s < h.S; ++s) {
+        const int R = 1 << h.lr[s], Ns = 1 << h.lns[s];
+        for (int t = 1; t < R; ++t)
+            for (int k = 0; k < Ns; ++k) out[off + (t - 1) * Ns + k] = omega_f32((int64_t)t * k, (int64_t)Ns * R);
+        off += (R - 1) * Ns;
+    }
+}
+
+}  // namespace fftc
+
+// ---------------------------------------------------------------------------
+// error state and plan registry
+// ---------------------------------------------------------------------------
+static thread_local fftc_status g_last_error = FFTC_OK;
+static std::mutex g_mu;
+static std::set<fftc_plan_s *> *g_live = nullptr;  // intentionally leaked: safe at exit
+
+static void register_plan(fftc_plan_s *p) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_live) g_live = new std::set<fftc_plan_s *>();
+    g_live->insert(p);
+}
+static bool is_live(const fftc_plan_s *p) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return p && g_live && g_live->count(const_cast<fftc_plan_s *>(p)) && p->magic == FFTC_PLAN_MAGIC;
+}
+static bool unregister_plan(fftc_plan_s *p) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_live || !g_live->count(p)) return false;
+    g_live->erase(p);
+    return true;
+}
+
+static fftc_plan fail(fftc_status s, fftc_plan_s *p = nullptr) {
+    g_last_error = s;
+    if (p) plan_free_device(p), delete p;
+    return nullptr;
+}
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+static int log2i(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << r) < v) ++r;
+    return r;
+}
+
+namespace fftc {
+
+void plan_free_device(fftc_plan_s *p) {
+    for (void *ptr : p->dev_allocs) cudaFree(ptr);
+    p->dev_allocs.clear();
+}
+
+cudaError_t plan_alloc(fftc_plan_s *p, size_t bytes, void **out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e == cudaSuccess) p->dev_allocs.push_back(*out);
+    return e;
+}
+
+cudaError_t plan_upload(fftc_plan_s *p, const void *host, size_t bytes, void **out) {
+    cudaError_t e = plan_alloc(p, bytes, out);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*out, host, bytes, cudaMemcpyHostToDevice);
+}
+
+}  // namespace fftc
+
+extern "C" {
+
+fftc_status fftc_get_last_error(void) { return g_last_error; }
+
+const char *fftc_status_string(fftc_status s) {
+    switch (s) {
+        case FFTC_OK: return "FFTC_OK";
+        case FFTC_ERR_INVALID_VALUE: return "FFTC_ERR_INVALID_VALUE";
+        case FFTC_ERR_UNSUPPORTED_SIZE: return "FFTC_ERR_UNSUPPORTED_SIZE";
+        case FFTC_ERR_MISALIGNED: return "FFTC_ERR_MISALIGNED";
+        case FFTC_ERR_ALLOC: return "FFTC_ERR_ALLOC";
+        case FFTC_ERR_CUDA: return "FFTC_ERR_CUDA";
+        case FFTC_ERR_INVALID_PLAN: return "FFTC_ERR_INVALID_PLAN";
+        case FFTC_ERR_TIMEOUT: return "FFTC_ERR_TIMEOUT";
+    }
+    return "FFTC_ERR_UNKNOWN";
+}
+
+fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_direction direction,
+                           fftc_precision precision) {
+    if (layout != FFTC_LAYOUT_INTERLEAVED && layout != FFTC_LAYOUT_SPLIT) return fail(FFTC_ERR_INVALID_VALUE);
+    if (direction != FFTC_FORWARD && direction != FFTC_INVERSE) return fail(FFTC_ERR_INVALID_VALUE);
+    if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_BF16_TC_SPLIT)
+        return fail(FFTC_ERR_INVALID_VALUE);
+    if (batch < 0) return fail(FFTC_ERR_INVALID_VALUE);
+    if (!is_pow2(n) || n < 2 || n > (int64_t(1) << 20)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    if (batch > (int64_t(1) << 40) / n) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+
+    fftc_plan_s *p = new (std::nothrow) fftc_plan_s();
+    if (!p) return fail(FFTC_ERR_ALLOC);
+    p->magic = FFTC_PLAN_MAGIC;
+    p->n = n;
+    p->logn = log2i(n);
+    p->batch = batch;
+    p->layout = layout;
+    p->direction = direction;
+    p->precision = precision;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(FFTC_ERR_CUDA, p);
+
+    fftc_status st = plan_build(p);
+    if (st != FFTC_OK) return fail(st, p);
+    register_plan(p);
+    g_last_error = FFTC_OK;
+    return p;
+}
+
+fftc_status fftc_destroy(fftc_plan plan) {
+    if (!plan) return FFTC_OK;
+    if (!unregister_plan(plan)) return FFTC_ERR_INVALID_PLAN;
+    plan_destroy_extra(plan);
+    plan_probe_free(plan);
+    plan_free_device(plan);
+    plan->magic = 0;
+    delete plan;
+    return FFTC_OK;
+}
+
+int64_t fftc_plan_bytes(fftc_plan plan) {
+    if (!is_live(plan)) return 0;
+    return plan->total_elems * 8;
+}
+
+fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    if (passes) *passes = plan->npasses;
+    int cnt = 0;
+    int tmp[32];
+    for (int i = 0; i < plan->npasses; ++i) {
+        const PassPlan &pp = plan->pass[i];
+        HostSched h = host_sched(pp.logl, pp.loge);
+        for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];
+    }
+    if (radices)
+        for (int i = 0; i < cnt && i < 16; ++i) radices[i] = tmp[i];
+    if (n_radices) *n_radices = cnt;
+    return FFTC_OK;
+}
+
+fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    if (plan->total_elems == 0) return FFTC_OK;
+    if (!in || !out) return FFTC_ERR_INVALID_VALUE;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return FFTC_ERR_MISALIGNED;
+    return plan_run(plan, in, out, nullptr, 0.f, (cudaStream_t)stream);
+}
+
+fftc_status fftc_execute_pointwise(fftc_plan plan, const void *in, void *out, const float *h, float scale,
+                                   void *stream) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    if (plan->uneven || plan->precision != FFTC_FP32) return FFTC_ERR_INVALID_VALUE;
+    if (plan->total_elems == 0) return FFTC_OK;
+    if (!in || !out || !h) return FFTC_ERR_INVALID_VALUE;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15) ||
+        (reinterpret_cast<uintptr_t>(h) & 15))
+        return FFTC_ERR_MISALIGNED;
+    return plan_run(plan, in, out, h, scale, (cudaStream_t)stream);
+}
+
+fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_out, void *dev_buf, void *stream) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    if (plan->total_elems == 0) return FFTC_OK;
+    if (!host_in || !host_out || !dev_buf) return FFTC_ERR_INVALID_VALUE;
+    if (reinterpret_cast<uintptr_t>(dev_buf) & 15) return FFTC_ERR_MISALIGNED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)plan->total_elems * 8;
+    if (cudaMemcpyAsync(dev_buf, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    fftc_status s = plan_run(plan, dev_buf, dev_buf, nullptr, 0.f, st);
+    if (s != FFTC_OK) return s;
+    if (cudaMemcpyAsync(host_out, dev_buf, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FFTC_ERR_CUDA;
+    return FFTC_OK;
+}
+
+fftc_status fftc_plan_timing(fftc_plan plan, int enable) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    plan_probe_free(plan);
+    if (!enable) return FFTC_OK;
+    const int slots = 4096;
+    try {
+        plan->probe_events.resize((size_t)3 * slots);
+    } catch (...) {
+        return FFTC_ERR_ALLOC;
+    }
+    for (size_t i = 0; i < plan->probe_events.size(); ++i) {
+        if (cudaEventCreate(&plan->probe_events[i]) != cudaSuccess) {
+            plan->probe_events.resize(i);
+            plan_probe_free(plan);
+            return FFTC_ERR_CUDA;
+        }
+    }
+    plan->probe_slots = slots;
+    plan->probe_used = 0;
+    plan->probe_on = true;
+    return FFTC_OK;
+}
+
+fftc_status fftc_plan_pass_times(fftc_plan plan, double *ms_per_pass, int *executes) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    double acc[2] = {0.0, 0.0};
+    const int np = plan->npasses > 0 ? plan->npasses : 1;
+    for (int s = 0; s < plan->probe_used; ++s) {
+        cudaEvent_t *ev = &plan->probe_events[(size_t)3 * s];
+        for (int i = 0; i < np && i < 2; ++i) {
+            if (cudaEventSynchronize(ev[i + 1]) != cudaSuccess) return FFTC_ERR_CUDA;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess) return FFTC_ERR_CUDA;
+            acc[i] += ms;
+        }
+    }
+    if (ms_per_pass) {
+        ms_per_pass[0] = acc[0];
+        ms_per_pass[1] = acc[1];
+    }
+    if (executes) *executes = plan->probe_used;
+    return FFTC_OK;
+}
+
+fftc_status fftc_plan_check(fftc_plan plan, void *stream) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    return plan_check_errors(plan, (cudaStream_t)stream);
+}
+
+}  // extern "C"

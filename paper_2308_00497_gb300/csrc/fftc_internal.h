@@ -1,0 +1,68 @@
+// Internal declarations shared by the planner (fftc_api.cu) and the kernel
+// instantiation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftc {
+
+enum PassKind : int {
+    KIND_ROWS = 0,   // whole transforms, contiguous lines in and out (single HBM pass)
+    KIND_COLS = 1,   // four-step pass 1: column FFTs at stride K, times w_N^(b t'), in place
+    KIND_ROWST = 2,  // four-step pass 2: row FFTs, written transposed (stride M)
+};
+
+enum LayoutId : int { LAYOUT_IL = 0, LAYOUT_SPLIT = 1 };
+
+// Arguments of one fused Stockham pass. A pass transforms `total_lines` lines of
+// length L; line g belongs to transform g >> log_lpt and is line g & (lpt - 1)
+// inside it. Element a of line g sits at complex offset
+//     (g >> log_lpt) * tr + (g & (lpt - 1)) * line + a * elem
+// in the input (in_*) and output (out_*) arrays. Split-layout arrays keep the
+// imaginary plane `plane` floats after the real one.
+struct PassParams {
+    const float *in;
+    float *out;
+    int64_t in_plane, out_plane;
+    int64_t total_lines;
+    int64_t in_tr, in_line, in_elem;
+    int64_t out_tr, out_line, out_elem;
+    const float2 *tw;      // per-stage tables of this pass (Sched layout)
+    const float2 *tw2_lo;  // inter-pass twiddle w_N^m = tw2_lo[m & lo_mask] * tw2_hi[m >> lo_bits]
+    const float2 *tw2_hi;
+    const float *post_h;   // optional real factor per output frequency (NULL = none)
+    int64_t post_line_mul, post_elem_mul;  // frequency = line * post_line_mul + a * post_elem_mul
+    float post_scale;
+    int32_t log_lpt;
+    int32_t log_n2;        // log2 N of the inter-pass twiddle (COLS only)
+    int32_t tw2_lo_bits;
+    int32_t conj_in, conj_out;  // conjugate on load / on store (inverse = conj F conj)
+};
+
+typedef cudaError_t (*LaunchFn)(const PassParams &, cudaStream_t);
+typedef cudaError_t (*PrepareFn)();
+
+struct KernelEntry {
+    int kind, logl, loge, lines, lin, lout;
+    int threads;
+    int smem_bytes;
+    LaunchFn launch;
+    PrepareFn prepare;
+};
+
+// Registry of compiled pass kernels (one table per instantiation unit).
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout);
+int kernel_count();
+const KernelEntry *kernel_at(int i);
+
+// Host-side mirror of the device radix schedule (Sched<LOGL, LOGE>).
+struct HostSched {
+    int S;
+    int lr[32];
+    int lns[32];
+    int tw_total;
+};
+HostSched host_sched(int logl, int loge);
+
+}  // namespace fftc

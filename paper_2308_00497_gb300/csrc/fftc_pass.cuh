@@ -1,0 +1,207 @@
+// The fused Stockham pass kernel.
+//
+// One CTA transforms C lines of length L = 2^LOGL held in registers (E = 2^LOGE
+// complex values per thread) and exchanged through shared memory between radix
+// stages. Each stage is one factor of the paper's Eq. 1 applied to every
+// sub-transform at once:
+//   read   a[t] = x[j + t L/R]                      (the stride permutation Pi)
+//   twiddle a[t] *= w_{Ns R}^{t (j mod Ns)}          (the diagonal D, Table 1 "Mul")
+//   butterfly a = DFT_R a                            (I (x) DFT_R, Table 1 FusedIKMV/MKIV)
+//   write  y[(j/Ns) Ns R + j mod Ns + t Ns] = a[t]   (Stockham autosort)
+// The first stage reads HBM directly and the last one writes HBM directly, both
+// coalesced, so one pass moves each element through HBM once.
+//
+// Thread <-> (line c, position tau) mapping, chosen per stage:
+//   tau-fast: consecutive threads walk one line (coalesced for contiguous lines);
+//   c-fast:   consecutive threads walk C lines at the same position (coalesced for
+//             column access at unit line stride; conflict-free in shared memory
+//             because the line pitch L + 1 is odd).
+#pragma once
+
+#include "fftc_device.cuh"
+#include "fftc_internal.h"
+
+namespace fftc {
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+struct Pass {
+    using Sc = Sched<LOGL, LOGE>;
+    static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
+    static constexpr int NT = C * TPL;
+    static constexpr int PITCH = (C > 1) ? L + 1 : L;
+    static constexpr int SMEM = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
+    static constexpr bool IN_TAU = (KIND != KIND_COLS);
+    static constexpr bool OUT_TAU = (KIND == KIND_ROWS);
+    static constexpr bool MID_TAU = (C < 16);
+    static_assert(S > 1 || IN_TAU == OUT_TAU, "a single-stage pass cannot change its mapping");
+    static_assert(NT >= 32 && NT <= 1024, "CTA size out of range");
+    __host__ __device__ static constexpr bool tau_fast(int s) {
+        return s == 0 ? IN_TAU : (s == S - 1 ? OUT_TAU : MID_TAU);
+    }
+    static constexpr bool all_tau() {
+        for (int s = 0; s < S; ++s)
+            if (!tau_fast(s)) return false;
+        return true;
+    }
+    // a line never leaves one warp: warp-level barriers are enough
+    static constexpr bool WARP_SYNC = all_tau() && TPL <= 32 && (32 % TPL) == 0;
+    static constexpr int REG_TARGET = E >= 32 ? 128 : (E >= 16 ? 80 : 64);
+    static constexpr int MINB = (65536 / (NT * REG_TARGET)) > 0 ? (65536 / (NT * REG_TARGET)) : 1;
+
+    __device__ __forceinline__ static void sync() {
+        if constexpr (WARP_SYNC)
+            __syncwarp();
+        else
+            __syncthreads();
+    }
+
+    __device__ __forceinline__ static int64_t line_off(int64_t g, int log_lpt, int64_t tr, int64_t line) {
+        return (g >> log_lpt) * tr + (g & ((int64_t(1) << log_lpt) - 1)) * line;
+    }
+
+    template <int R>
+    __device__ __forceinline__ static void load_global(const PassParams &p, float2 (&v)[E], int tau, int64_t g,
+                                                       bool live) {
+        const int64_t base = line_off(g, p.log_lpt, p.in_tr, p.in_line);
+#pragma unroll
+        for (int q = 0; q < E / R; ++q) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int a = tau + q * TPL + t * (L / R);
+                const int64_t off = base + (int64_t)a * p.in_elem;
+                float2 x = make_float2(0.f, 0.f);
+                if (live) {
+                    if constexpr (LIN == LAYOUT_IL) {
+                        x = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
+                    } else {
+                        x.x = __ldcs(p.in + off);
+                        x.y = __ldcs(p.in + p.in_plane + off);
+                    }
+                }
+                if (p.conj_in) x.y = -x.y;
+                v[q * R + t] = x;
+            }
+        }
+    }
+
+    template <int R>
+    __device__ __forceinline__ static void store_global(const PassParams &p, float2 (&v)[E], int tau, int64_t g,
+                                                        bool live) {
+        if (!live) return;
+        const int64_t l = g & ((int64_t(1) << p.log_lpt) - 1);
+        const int64_t base = line_off(g, p.log_lpt, p.out_tr, p.out_line);
+#pragma unroll
+        for (int q = 0; q < E / R; ++q) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int a = tau + q * TPL + t * (L / R);
+                float2 x = v[q * R + t];
+                if constexpr (KIND == KIND_COLS) {
+                    // inter-pass twiddle of Eq. 1 applied at the memory level: w_N^(b t')
+                    const int64_t m = (l * a) & ((int64_t(1) << p.log_n2) - 1);
+                    const float2 w = cmul(__ldg(p.tw2_lo + (m & ((int64_t(1) << p.tw2_lo_bits) - 1))),
+                                          __ldg(p.tw2_hi + (m >> p.tw2_lo_bits)));
+                    x = cmul(x, w);
+                }
+                if (p.post_h) {
+                    const float h = __ldg(p.post_h + l * p.post_line_mul + (int64_t)a * p.post_elem_mul) * p.post_scale;
+                    x.x *= h;
+                    x.y *= h;
+                }
+                if (p.conj_out) x.y = -x.y;
+                const int64_t off = base + (int64_t)a * p.out_elem;
+                if constexpr (LOUT == LAYOUT_IL) {
+                    __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
+                } else {
+                    __stcs(p.out + off, x.x);
+                    __stcs(p.out + p.out_plane + off, x.y);
+                }
+            }
+        }
+    }
+
+    template <int s>
+    __device__ __forceinline__ static void stage(const PassParams &p, float2 *sm, float2 (&v)[E], int tid, int64_t g0) {
+        constexpr int LR = Sc::lr(s), R = 1 << LR, LNS = Sc::lns(s), NS = 1 << LNS;
+        constexpr bool TF = tau_fast(s);
+        const int c = TF ? tid / TPL : tid % C;
+        const int tau = TF ? tid % TPL : tid / C;
+        const int64_t g = g0 + c;
+        const bool live = g < p.total_lines;
+        float2 *line = sm + c * PITCH;
+
+        if constexpr (s == 0) {
+            load_global<R>(p, v, tau, g, live);
+        } else {
+            constexpr int PLO = Sc::lns(s - 1);
+#pragma unroll
+            for (int q = 0; q < E / R; ++q) {
+#pragma unroll
+                for (int t = 0; t < R; ++t) v[q * R + t] = line[swz(tau + q * TPL + t * (L / R), PLO, LNS)];
+            }
+            const float2 *tw = p.tw + Sc::tw_off(s);
+#pragma unroll
+            for (int q = 0; q < E / R; ++q) {
+                const int k = (tau + q * TPL) & (NS - 1);
+#pragma unroll
+                for (int t = 1; t < R; ++t) v[q * R + t] = cmul(v[q * R + t], __ldg(tw + (t - 1) * NS + k));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E / R; ++q) dft<R>(v + q * R);
+
+        if constexpr (s < S - 1) {
+            if constexpr (s > 0) sync();  // every read of this stage precedes any overwrite
+#pragma unroll
+            for (int q = 0; q < E / R; ++q) {
+                const int j = tau + q * TPL;
+                const int b = ((j >> LNS) << (LNS + LR)) + (j & (NS - 1));
+#pragma unroll
+                for (int t = 0; t < R; ++t) line[swz(b + t * NS, LNS, LNS + LR)] = v[q * R + t];
+            }
+            sync();
+            stage<s + 1>(p, sm, v, tid, g0);
+        } else {
+            store_global<R>(p, v, tau, g, live);
+        }
+    }
+
+    __device__ __forceinline__ static void run(const PassParams &p) {
+        extern __shared__ float2 sm_dyn[];
+        float2 v[E];
+        stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
+    }
+};
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT>::NT, Pass<LOGL, LOGE, C, KIND, LIN, LOUT>::MINB)
+    k_pass(const __grid_constant__ PassParams p) {
+    Pass<LOGL, LOGE, C, KIND, LIN, LOUT>::run(p);
+}
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+cudaError_t launch_pass(const PassParams &p, cudaStream_t st) {
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
+    const int64_t blocks = (p.total_lines + C - 1) / C;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+cudaError_t prepare_pass() {
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
+    if (P::SMEM <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                P::SMEM);
+}
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+constexpr KernelEntry entry() {
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
+    return KernelEntry{KIND, LOGL, LOGE, C, LIN, LOUT, P::NT, P::SMEM,
+                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT>};
+}
+
+}  // namespace fftc

@@ -1,0 +1,267 @@
+// Planner and executor of the FP32 Stockham path.
+//
+// n <= 2^13: one fused pass (KIND_ROWS), each CTA transforming whole rows.
+// n >  2^13: Eq. 1 applied once at the HBM level, n = M * K (four-step):
+//   pass 1 (KIND_COLS):  K column FFTs of length M over x[t*K + b], times w_n^(b t'),
+//                        written in place to the workspace z[t'*K + b];
+//   pass 2 (KIND_ROWST): M row FFTs of length K over z[t'*K .. t'*K + K), written
+//                        transposed to X[b'*M + t'] (natural order).
+// Inverse transforms run the forward arithmetic on conj(x) and conjugate the
+// result (F^H x = conj(F conj x)), so both directions share every kernel.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "fftc_plan.h"
+
+namespace fftc {
+
+static const int kMaxSinglePassLog = 13;
+static const int kPassLines = 16;
+
+static int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    return atoi(v);
+}
+
+bool choose_rows(int logn, int lin, int *loge, int *lines) {
+    int e;
+    if (logn <= 4) e = logn;
+    else if (logn <= 8) e = 4;
+    else if (logn == 12) e = 4;
+    else e = 5;
+    char name[64];
+    snprintf(name, sizeof(name), "FFTC_TUNE_ROWS_E_%d", logn);
+    e = env_int(name, e);
+    if (e > logn) e = logn;
+    const int tpl = 1 << (logn - e);
+    int c = tpl >= 256 ? 1 : 256 / tpl;
+    snprintf(name, sizeof(name), "FFTC_TUNE_ROWS_C_%d", logn);
+    c = env_int(name, c);
+    *loge = e;
+    *lines = c;
+    return find_kernel(KIND_ROWS, logn, e, c, lin, lin) != nullptr;
+}
+
+bool choose_four_step(int logn, int *logm, int *loge1, int *loge2) {
+    int m = env_int("FFTC_TUNE_FOURSTEP_LOGM", logn / 2);
+    int k = logn - m;
+    *logm = m;
+    *loge1 = env_int("FFTC_TUNE_COLS_E", m >= 9 ? 5 : 4);
+    *loge2 = env_int("FFTC_TUNE_ROWST_E", k >= 9 ? 5 : 4);
+    if (*loge1 > m) *loge1 = m;
+    if (*loge2 >= k) *loge2 = k - 1;
+    return true;
+}
+
+static fftc_status upload_stage_tables(fftc_plan_s *p, PassPlan &pp) {
+    std::vector<float2> tw;
+    stage_twiddles(pp.logl, pp.loge, tw);
+    void *d = nullptr;
+    if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    pp.tw = (float2 *)d;
+    pp.base.tw = pp.tw;
+    return FFTC_OK;
+}
+
+static fftc_status prepare(PassPlan &pp) {
+    if (!pp.k) return FFTC_ERR_UNSUPPORTED_SIZE;
+    if (pp.k->prepare() != cudaSuccess) return FFTC_ERR_CUDA;
+    return FFTC_OK;
+}
+
+fftc_status plan_build_fp32(fftc_plan_s *p) {
+    const int64_t n = p->n, B = p->batch;
+    const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
+    const int64_t plane = (lay == LAYOUT_SPLIT) ? n * B : 0;
+    p->total_elems = n * B;
+    void *d = nullptr;
+    if (plan_alloc(p, 16, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->d_err = (int *)d;
+    if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
+
+    if (p->logn <= env_int("FFTC_TUNE_MAX_SINGLE_LOG", kMaxSinglePassLog)) {
+        PassPlan &pp = p->pass[0];
+        p->npasses = 1;
+        pp.kind = KIND_ROWS;
+        pp.logl = p->logn;
+        if (!choose_rows(p->logn, lay, &pp.loge, &pp.lines)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        pp.lin = pp.lout = lay;
+        pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay);
+        PassParams &b = pp.base;
+        memset(&b, 0, sizeof(b));
+        b.in_plane = b.out_plane = plane;
+        b.total_lines = B;
+        b.log_lpt = 0;
+        b.in_tr = b.out_tr = n;
+        b.in_line = b.out_line = 0;
+        b.in_elem = b.out_elem = 1;
+        b.post_line_mul = 0;
+        b.post_elem_mul = 1;
+        fftc_status s = upload_stage_tables(p, pp);
+        if (s != FFTC_OK) return s;
+        return prepare(pp);
+    }
+
+    // four-step: n = M * K
+    int logm, e1, e2;
+    if (!choose_four_step(p->logn, &logm, &e1, &e2)) return FFTC_ERR_UNSUPPORTED_SIZE;
+    const int logk = p->logn - logm;
+    const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
+    p->npasses = 2;
+    if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->workspace = (float2 *)d;
+
+    // inter-pass twiddle w_n^m as a product of two small tables
+    p->tw2_lo_bits = (p->logn + 1) / 2;
+    const int64_t nlo = int64_t(1) << p->tw2_lo_bits, nhi = n >> p->tw2_lo_bits;
+    std::vector<float2> lo(nlo), hi(nhi);
+    for (int64_t m = 0; m < nlo; ++m) {
+        double c, s;
+        unit_root(m, n, &c, &s);
+        lo[m] = make_float2((float)c, (float)-s);
+    }
+    for (int64_t m = 0; m < nhi; ++m) {
+        double c, s;
+        unit_root(m * nlo, n, &c, &s);
+        hi[m] = make_float2((float)c, (float)-s);
+    }
+    if (plan_upload(p, lo.data(), lo.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->tw2_lo = (float2 *)d;
+    if (plan_upload(p, hi.data(), hi.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->tw2_hi = (float2 *)d;
+
+    {   // pass 1: columns
+        PassPlan &pp = p->pass[0];
+        pp.kind = KIND_COLS;
+        pp.logl = logm;
+        pp.loge = e1;
+        pp.lines = kPassLines;
+        pp.lin = lay;
+        pp.lout = LAYOUT_IL;
+        pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout);
+        PassParams &b = pp.base;
+        memset(&b, 0, sizeof(b));
+        b.in_plane = plane;
+        b.out_plane = 0;
+        b.total_lines = B * K;
+        b.log_lpt = logk;
+        b.in_tr = n;
+        b.in_line = 1;
+        b.in_elem = K;
+        b.out_tr = n;
+        b.out_line = 1;
+        b.out_elem = K;
+        b.tw2_lo = p->tw2_lo;
+        b.tw2_hi = p->tw2_hi;
+        b.log_n2 = p->logn;
+        b.tw2_lo_bits = p->tw2_lo_bits;
+        fftc_status s = upload_stage_tables(p, pp);
+        if (s != FFTC_OK) return s;
+        if ((s = prepare(pp)) != FFTC_OK) return s;
+    }
+    {   // pass 2: rows, transposed store
+        PassPlan &pp = p->pass[1];
+        pp.kind = KIND_ROWST;
+        pp.logl = logk;
+        pp.loge = e2;
+        pp.lines = kPassLines;
+        pp.lin = LAYOUT_IL;
+        pp.lout = lay;
+        pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout);
+        PassParams &b = pp.base;
+        memset(&b, 0, sizeof(b));
+        b.in_plane = 0;
+        b.out_plane = plane;
+        b.total_lines = B * M;
+        b.log_lpt = logm;
+        b.in_tr = n;
+        b.in_line = K;
+        b.in_elem = 1;
+        b.out_tr = n;
+        b.out_line = 1;
+        b.out_elem = M;
+        b.post_line_mul = 1;
+        b.post_elem_mul = M;
+        fftc_status s = upload_stage_tables(p, pp);
+        if (s != FFTC_OK) return s;
+        if ((s = prepare(pp)) != FFTC_OK) return s;
+    }
+    return FFTC_OK;
+}
+
+fftc_status plan_build_tc(fftc_plan_s *p);  // fftc_tc.cu
+
+fftc_status plan_build(fftc_plan_s *p) {
+    if (p->precision == FFTC_FP32) return plan_build_fp32(p);
+    return plan_build_tc(p);
+}
+
+fftc_status plan_run_tc(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);  // fftc_tc.cu
+
+fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
+                     cudaStream_t st) {
+    if (p->uneven) return FFTC_ERR_INVALID_PLAN;  // uneven plans run through fftc_uneven.cu
+    if (p->precision != FFTC_FP32) {
+        if (post_h) return FFTC_ERR_INVALID_VALUE;
+        return plan_run_tc(p, in, out, st);
+    }
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    cudaEvent_t *ev = nullptr;
+    if (p->probe_on && p->probe_used < p->probe_slots) ev = &p->probe_events[(size_t)3 * p->probe_used++];
+    if (ev) cudaEventRecord(ev[0], st);
+    if (p->npasses == 1) {
+        PassParams a = p->pass[0].base;
+        a.in = (const float *)in;
+        a.out = (float *)out;
+        a.conj_in = a.conj_out = inv;
+        a.post_h = post_h;
+        a.post_scale = post_scale;
+        if (p->pass[0].k->launch(a, st) != cudaSuccess) return FFTC_ERR_CUDA;
+        if (ev) cudaEventRecord(ev[1], st);
+        return FFTC_OK;
+    }
+    PassParams a = p->pass[0].base;
+    a.in = (const float *)in;
+    a.out = (float *)p->workspace;
+    a.conj_in = inv;
+    a.conj_out = 0;
+    if (p->pass[0].k->launch(a, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (ev) cudaEventRecord(ev[1], st);
+    PassParams b = p->pass[1].base;
+    b.in = (const float *)p->workspace;
+    b.out = (float *)out;
+    b.conj_in = 0;
+    b.conj_out = inv;
+    b.post_h = post_h;
+    b.post_scale = post_scale;
+    if (p->pass[1].k->launch(b, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (ev) cudaEventRecord(ev[2], st);
+    return FFTC_OK;
+}
+
+void plan_probe_free(fftc_plan_s *p) {
+    for (cudaEvent_t e : p->probe_events) cudaEventDestroy(e);
+    p->probe_events.clear();
+    p->probe_slots = p->probe_used = 0;
+    p->probe_on = false;
+}
+
+fftc_status plan_check_errors(fftc_plan_s *p, cudaStream_t st) {
+    if (!p->d_err) return FFTC_OK;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (h) {
+        if (cudaMemsetAsync(p->d_err, 0, sizeof(int), st) != cudaSuccess) return FFTC_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return FFTC_ERR_CUDA;
+        return FFTC_ERR_TIMEOUT;
+    }
+    return FFTC_OK;
+}
+
+}  // namespace fftc

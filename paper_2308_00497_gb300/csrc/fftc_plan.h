@@ -1,0 +1,75 @@
+// The plan object behind the opaque fftc_plan handle, and the planner entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fftc.h"
+#include "fftc_internal.h"
+
+#define FFTC_PLAN_MAGIC 0x66667463u
+
+namespace fftc {
+
+struct PassPlan {
+    int kind, logl, loge, lines, lin, lout;
+    const KernelEntry *k;
+    float2 *tw;       // device stage tables of this pass
+    PassParams base;  // everything but the data pointers, conjugation and epilogue
+};
+
+struct UnevenState;  // persistent uneven-batch executor (fftc_uneven.cu)
+struct TcState;      // tensor-core radix-16 executor (fftc_tc.cu)
+
+}  // namespace fftc
+
+struct fftc_plan_s {
+    uint32_t magic = 0;
+    int device = 0;
+    int64_t n = 0;
+    int logn = 0;
+    int64_t batch = 0;
+    int64_t total_elems = 0;  // complex elements per buffer
+    fftc_layout layout = FFTC_LAYOUT_INTERLEAVED;
+    fftc_direction direction = FFTC_FORWARD;
+    fftc_precision precision = FFTC_FP32;
+    int npasses = 0;
+    fftc::PassPlan pass[2] = {};
+    float2 *workspace = nullptr;
+    float2 *tw2_lo = nullptr, *tw2_hi = nullptr;
+    int tw2_lo_bits = 0;
+    int *d_err = nullptr;  // device error word (bounded waits)
+    fftc::UnevenState *uneven = nullptr;
+    fftc::TcState *tc = nullptr;
+    std::vector<void *> dev_allocs;
+    // timing probe: events[slot * 3 + i] before pass i (i < npasses) and after the last
+    std::vector<cudaEvent_t> probe_events;
+    int probe_slots = 0, probe_used = 0;
+    bool probe_on = false;
+};
+
+namespace fftc {
+
+fftc_status plan_build(fftc_plan_s *p);
+// Enqueue the plan on `st`. post_h (device, n floats, may be NULL) multiplies every
+// output frequency k by post_h[k] * post_scale.
+fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
+                     cudaStream_t st);
+fftc_status plan_check_errors(fftc_plan_s *p, cudaStream_t st);
+void plan_destroy_extra(fftc_plan_s *p);
+void plan_probe_free(fftc_plan_s *p);
+void plan_free_device(fftc_plan_s *p);
+cudaError_t plan_alloc(fftc_plan_s *p, size_t bytes, void **out);
+cudaError_t plan_upload(fftc_plan_s *p, const void *host, size_t bytes, void **out);
+
+void unit_root(int64_t m, int64_t L, double *cosv, double *sinv);
+void stage_twiddles(int logl, int loge, std::vector<float2> &out);
+
+// Kernel choice for a pass; overridable through FFTC_TUNE_* environment variables
+// by the tuner. Returns false if no compiled kernel fits.
+bool choose_rows(int logn, int lin, int *loge, int *lines);
+bool choose_four_step(int logn, int *logm, int *loge1, int *loge2);
+
+}  // namespace fftc

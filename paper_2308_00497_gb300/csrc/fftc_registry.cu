@@ -1,0 +1,33 @@
+// Registry of every compiled pass kernel, gathered from the instantiation units.
+#include "fftc_internal.h"
+
+namespace fftc {
+
+extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[];
+extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount;
+
+struct TableRef {
+    const KernelEntry *t;
+    const int *n;
+};
+static const TableRef kTables[] = {
+    {kRowsIlTable, &kRowsIlCount}, {kRowsSplitTable, &kRowsSplitCount},
+    {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
+};
+
+int kernel_count() {
+    int c = 0;
+    for (const TableRef &r : kTables) c += *r.n;
+    return c;
+}
+
+const KernelEntry *kernel_at(int i) {
+    if (i < 0) return nullptr;
+    for (const TableRef &r : kTables) {
+        if (i < *r.n) return &r.t[i];
+        i -= *r.n;
+    }
+    return nullptr;
+}
+
+}  // namespace fftc

@@ -1,0 +1,77 @@
+"""The C ABI loads and exports every symbol include/fftc.h declares; argument
+validation that needs no device (bad sizes, bad enums, NULL and stale plans)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fftc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_00497_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fftc_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_symbol(lib):
+    from paper_2308_00497_gb300 import _native
+    assert set(declared_functions()) == set(_native.PROTOTYPES)
+
+
+def test_status_strings(lib):
+    from paper_2308_00497_gb300 import _native as nat
+    names = [nat.status_string(i) for i in range(8)]
+    assert names[0] == "FFTC_OK" and names[7] == "FFTC_ERR_TIMEOUT"
+    assert len(set(names)) == 8
+    assert nat.status_string(99) == "FFTC_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 12, 1000, 1 << 21, -8])
+def test_unsupported_sizes_rejected_before_any_device_call(lib, n):
+    from paper_2308_00497_gb300 import _native as nat
+    assert not lib.fftc_plan_create(n, 4, 0, -1, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
+
+
+@pytest.mark.parametrize("args", [(64, -1, 0, -1, 0), (64, 4, 2, -1, 0), (64, 4, 0, 0, 0), (64, 4, 0, -1, 9)])
+def test_bad_arguments_rejected(lib, args):
+    from paper_2308_00497_gb300 import _native as nat
+    assert not lib.fftc_plan_create(*args)
+    assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE
+
+
+def test_null_and_foreign_plans(lib):
+    from paper_2308_00497_gb300 import _native as nat
+    assert lib.fftc_destroy(None) == nat.OK
+    bogus = ctypes.c_void_p(0x1000)
+    assert lib.fftc_destroy(bogus) == nat.ERR_INVALID_PLAN
+    assert lib.fftc_execute(None, None, None, None) == nat.ERR_INVALID_PLAN
+    assert lib.fftc_execute(bogus, None, None, None) == nat.ERR_INVALID_PLAN
+    assert lib.fftc_plan_bytes(bogus) == 0
+    assert lib.fftc_plan_info(bogus, None, None, None) == nat.ERR_INVALID_PLAN
+    assert lib.fftc_plan_check(None, None) == nat.ERR_INVALID_PLAN
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2308_00497_gb300 import _native as nat
+    monkeypatch.setattr(nat, "_lib", None)
+    monkeypatch.setattr(nat, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        nat.load()

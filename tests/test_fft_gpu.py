@@ -1,0 +1,153 @@
+"""Parity of the FP32 CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: per-transform relative L2 error <= 2e-6 * log2(n) against the oracle on the
+same seeded inputs (the benchmark spec's tolerance for FP32), for every supported n,
+both layouts (Section 3, step 3) and both directions; ragged batches so that
+the last CTA tile is partial; full-size sweep batches (n * batch = 2^26) on
+sampled rows; bitwise determinism.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic_inputs as si
+from gpu_util import from_device, rel_l2_rows, to_device, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2308_00497_gb300 import build
+    build.build()
+
+
+def _batch_for(n):
+    if n <= 16:
+        return 300   # tiles of 128 lines: two full tiles and a tail
+    if n <= 512:
+        return 37
+    if n <= 4096:
+        return 7
+    if n <= 1 << 14:
+        return 3
+    return 2
+
+
+def _run(x, layout, inverse):
+    import paper_2308_00497_gb300 as fc
+    t = to_device(x, layout)
+    y = fc.ifft(t, layout=layout) if inverse else fc.fft(t, layout=layout)
+    torch.cuda.synchronize()
+    return from_device(y, layout)
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("e", list(range(1, 21)))
+def test_parity_all_sizes(e, inverse, layout):
+    n = 1 << e
+    B = _batch_for(n)
+    x = si.uniform_complex(B, n, seed=1000 + e)
+    y = _run(x, layout, inverse)
+    ref = oracle.fft(x.astype(np.complex128), inverse=inverse)
+    err = rel_l2_rows(y, ref)
+    assert err.max() <= tol_fp32(n), (n, float(err.max()))
+
+
+@pytest.mark.parametrize("e", [4, 8, 10, 12, 13, 14, 16, 20])
+def test_pure_tones(e):
+    """exp(+2 pi i k0 j / n) -> n delta_{k0} forward (closed form, no oracle needed)."""
+    n = 1 << e
+    x, k0 = si.tones(4, n, seed=7 + e)
+    y = _run(x, "interleaved", False)
+    want = np.zeros((4, n), np.complex128)
+    want[np.arange(4), k0] = n
+    assert rel_l2_rows(y, want).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [5, 10, 13, 14, 17])
+def test_roundtrip_and_inplace(e):
+    import paper_2308_00497_gb300 as fc
+    n = 1 << e
+    x = si.gaussian_complex(3, n, seed=e)
+    t = to_device(x, "interleaved")
+    keep = t.clone()
+    fwd = fc.get_plan(n, 3, "interleaved", False)
+    inv = fc.get_plan(n, 3, "interleaved", True)
+    fwd.execute(t, t)          # in place
+    inv.execute(t, t)
+    torch.cuda.synchronize()
+    err = rel_l2_rows(t.cpu().numpy(), n * keep.cpu().numpy())
+    assert err.max() <= 2 * tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [8, 12, 16, 20])
+def test_bitwise_determinism(e):
+    import paper_2308_00497_gb300 as fc
+    n = 1 << e
+    B = max(1, (1 << 22) // n)
+    x = to_device(si.uniform_complex(B, n, seed=3), "split")
+    p = fc.get_plan(n, B, "split", False)
+    a = p.execute(x)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = p.execute(x, stream=s)
+    s.synchronize()
+    c = p.execute(x)
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    assert torch.equal(a.view(torch.int32), c.view(torch.int32))
+
+
+@pytest.mark.parametrize("e", list(range(8, 21)))
+def test_full_size_sweep_sampled_rows(e):
+    """The benchmark's sweep shapes (n * batch = 2^26) in both layouts; rows sampled
+    (first, last and two random ones) are checked against the oracle."""
+    n = 1 << e
+    B = (1 << 26) // n
+    x = si.uniform_complex(B, n, seed=200 + e)
+    rows = np.unique(np.array([0, B - 1, *np.random.default_rng(e).integers(0, B, 2)]))
+    for layout, inverse in (("interleaved", False), ("split", True)):
+        y = _run(x, layout, inverse)
+        ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
+        err = rel_l2_rows(y[rows], ref)
+        assert err.max() <= tol_fp32(n), (n, layout, float(err.max()))
+        assert np.isfinite(y).all()
+
+
+def test_plan_info_and_bytes():
+    import paper_2308_00497_gb300 as fc
+    p = fc.Plan(1024, 4)
+    passes, radices = p.info()
+    assert passes == 1 and int(np.prod(radices)) == 1024
+    assert p.bytes() == 1024 * 4 * 8
+    q = fc.Plan(1 << 20, 1, "split", True)
+    passes, radices = q.info()
+    assert passes == 2 and int(np.prod(radices)) == 1 << 20
+
+
+def test_empty_batch_is_a_noop():
+    import paper_2308_00497_gb300 as fc
+    p = fc.Plan(256, 0)
+    x = torch.empty((0, 256), dtype=torch.complex64, device="cuda")
+    p.execute(x)
+    torch.cuda.synchronize()
+
+
+def test_misaligned_and_null_pointers():
+    from paper_2308_00497_gb300 import _native as nat
+    import paper_2308_00497_gb300 as fc
+    lib = nat.load()
+    p = fc.Plan(64, 2)
+    buf = torch.zeros(2 * 64 + 4, dtype=torch.complex64, device="cuda")
+    base = buf.data_ptr()
+    assert lib.fftc_execute(p.handle, ctypes.c_void_p(base + 8), ctypes.c_void_p(base + 16), None) == nat.ERR_MISALIGNED
+    assert lib.fftc_execute(p.handle, None, ctypes.c_void_p(base), None) == nat.ERR_INVALID_VALUE
+    h = lib.fftc_plan_create(64, 2, 0, -1, 0)
+    assert lib.fftc_destroy(h) == nat.OK
+    assert lib.fftc_destroy(h) == nat.ERR_INVALID_PLAN   # a destroyed plan is recognised
+    assert lib.fftc_execute(h, ctypes.c_void_p(base), ctypes.c_void_p(base), None) == nat.ERR_INVALID_PLAN
