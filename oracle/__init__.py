@@ -48,13 +48,18 @@ DIRECT_MAX_N = 4096
 
 def build_oracle(force: bool = False) -> str:
     """Compile ``fft_oracle.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    import platform
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    stamp = os.path.join(os.path.dirname(_LIB_PATH), "machine.txt")
+    other_host = (not os.path.exists(stamp)) or open(stamp).read().strip() != platform.machine()
+    stale = other_host or (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm", "-lpthread"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
+        with open(stamp, "w") as f:
+            f.write(platform.machine() + "\n")
     return _LIB_PATH
 
 

@@ -12,6 +12,7 @@ import argparse
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -51,6 +52,10 @@ def _compile(src: str, obj: str, extra: list[str]) -> tuple[str, str]:
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile and link libfftc.so; returns its path."""
     os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+    stamp = os.path.join(BUILD, "machine.txt")
+    machine = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != machine:
+        force = True  # objects from another host architecture are never reused
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = _headers_mtime()
     todo = []
@@ -75,6 +80,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
         if r.returncode != 0:
             raise RuntimeError(f"link of libfftc.so failed:\n{r.stderr}")
         os.replace(LIB + ".tmp", LIB)
+    with open(stamp, "w") as f:
+        f.write(machine + "\n")
     return LIB
 
 
