@@ -40,6 +40,7 @@ bool choose_rows(int logn, int lin, int *loge, int *lines) {
     if (e > logn) e = logn;
     const int tpl = 1 << (logn - e);
     int c = tpl >= 256 ? 1 : 256 / tpl;
+    if (logn <= 4) c = 128;  // one thread per line: 128-line CTAs
     snprintf(name, sizeof(name), "FFTC_TUNE_ROWS_C_%d", logn);
     c = env_int(name, c);
     *loge = e;
