@@ -161,6 +161,33 @@ fftc_status fftc_plan_timing(fftc_plan plan, int enable);
  */
 fftc_status fftc_plan_pass_times(fftc_plan plan, double *ms_per_pass, int *executes);
 
+/*
+ * Allocation-free two-pass transform. The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory themselves, such as a plugin
+ * running inside a host application whose caching allocator owns the whole GPU memory
+ * budget, or a loop that forbids any allocation once it has started. It needs no plan:
+ * it computes the same transforms as a plan of (n, batch, layout, direction, FFTC_FP32)
+ * with the four-step kernels, using a library-owned scratch buffer and twiddle tables
+ * that are fixed-size __device__ arrays inside libfftc.so. Those arrays (16 MiB of
+ * scratch plus about 224 KiB of tables) stay resident on every GPU that loads the
+ * library until the process exits.
+ *
+ *   n      power of two with 2^14 <= n <= 2^20 (the sizes that use a workspace);
+ *   batch  with n * batch <= 2^21 complex elements (the scratch capacity);
+ *          anything else returns FFTC_ERR_UNSUPPORTED_SIZE, batch < 0 FFTC_ERR_INVALID_VALUE;
+ *   in/out device pointers as in fftc_execute (16-byte aligned; in == out allowed).
+ *
+ * Calls no cudaMalloc, cudaFree or other allocating routine. The first call on a device
+ * sets that device up (looks up the arrays' device addresses with the device current,
+ * uploads the tables with a synchronous copy); make that first call before any stream
+ * capture. Every call on a device shares the one scratch array, which keeps the last
+ * call's contents (no call relies on it starting at zero: pass 1 overwrites every element
+ * that pass 2 reads), so calls that can overlap on the GPU (different streams, or a
+ * plan-free call racing another) corrupt each other's results: serialise them.
+ */
+fftc_status fftc_execute_noalloc(int64_t n, int64_t batch, fftc_layout layout, fftc_direction direction,
+                                 const void *in, void *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,7 @@ PROTOTYPES = {
     "fftc_execute_pointwise": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_float, _vp]),
     "fftc_plan_timing": (_c_int, [_vp, _c_int]),
     "fftc_plan_pass_times": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
+    "fftc_execute_noalloc": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _vp, _vp, _vp]),
 }
 
 _lib = None
