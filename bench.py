@@ -174,11 +174,11 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
     x = torch.from_numpy(x_host.view(np.float32)).to(dev)          # 2^27 floats
     y = torch.empty_like(x)
     plans = []
-    for e in SIZES:
+    for e in args.sizes:
         n = 1 << e
         B = ELEMS // n
-        for layout in LAYOUTS:
-            for inv in DIRECTIONS:
+        for layout in args.layouts:
+            for inv in args.dirs:
                 plans.append((e, layout, inv, fc.Plan(n, B, layout, inv, device=dev)))
 
     def views(layout, n, B):
@@ -271,7 +271,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = 0
         import oracle
-        rows = oracle.default_threads()
+        rows = 24 * oracle.default_threads()
         f, s, th = oracle_sample(rows)
         cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": th, "kind": "oracle",
                "sample": f"{rows} rows of each n=2^8..2^20 (forward, FP64); direct O(n^2) DFT for n<=4096, "
@@ -310,7 +310,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sizes", default=",".join(str(e) for e in SIZES),
+                    help="log2 n list (default: the whole sweep); a subset is for profiling only")
+    ap.add_argument("--layouts", default=",".join(LAYOUTS))
+    ap.add_argument("--dirs", default="fwd,inv")
     args = ap.parse_args()
+    args.sizes = [int(v) for v in args.sizes.split(",")]
+    args.layouts = args.layouts.split(",")
+    args.dirs = [d == "inv" for d in args.dirs.split(",")]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
