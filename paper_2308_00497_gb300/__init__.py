@@ -4,4 +4,4 @@ The transforms run in libfftc.so (C ABI: include/fftc.h); this package is its
 thin Python binding, with torch supplying device memory and streams.
 """
 from ._native import FftcError, load as load_library  # noqa: F401
-from .api import Plan, fft, get_plan, ifft  # noqa: F401
+from .api import Plan, UnevenPlan, fft, get_plan, ifft  # noqa: F401

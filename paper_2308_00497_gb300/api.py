@@ -122,6 +122,40 @@ class Plan:
             pass
 
 
+class UnevenPlan(Plan):
+    """Transforms of uneven lengths in one persistent launch (fftc_plan_create_uneven).
+
+    n[i] (powers of two in [64, 2^16]), direction[i] (-1 forward, +1 inverse) and
+    offset[i] (complex elements) describe row i of a flat complex64 buffer.
+    """
+
+    def __init__(self, n, direction, offset, device=None):
+        import numpy as np
+        lib = nat.load()
+        n = np.ascontiguousarray(n, dtype=np.int64)
+        d = np.ascontiguousarray(direction, dtype=np.int8)
+        o = np.ascontiguousarray(offset, dtype=np.int64)
+        if not (n.shape == d.shape == o.shape) or n.ndim != 1:
+            raise ValueError("n, direction and offset must be 1-D arrays of one length")
+        self.n_rows = int(n.size)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.layout, self.precision = "interleaved", "fp32"
+        with torch.cuda.device(self.device):
+            h = lib.fftc_plan_create_uneven(self.n_rows, n.ctypes.data, d.ctypes.data, o.ctypes.data,
+                                            nat.LAYOUT_INTERLEAVED, nat.FP32)
+        if not h:
+            raise nat.FftcError(lib.fftc_get_last_error(), f"fftc_plan_create_uneven(count={self.n_rows})")
+        self._h = ctypes.c_void_p(h)
+        self.total = int(lib.fftc_plan_bytes(self._h)) // 8
+
+    def _check_tensor(self, t: torch.Tensor, name: str):
+        if t.dtype != torch.complex64 or t.dim() != 1 or t.numel() < self.total or not t.is_contiguous() \
+                or t.device != self.device:
+            raise ValueError(f"{name}: expected a contiguous complex64 vector of >= {self.total} elements "
+                             f"on {self.device}")
+
+
 _cache: dict = {}
 _cache_lock = threading.Lock()
 

@@ -129,7 +129,11 @@ static bool unregister_plan(fftc_plan_s *p) {
 
 static fftc_plan fail(fftc_status s, fftc_plan_s *p = nullptr) {
     g_last_error = s;
-    if (p) plan_free_device(p), delete p;
+    if (p) {
+        plan_destroy_extra(p);
+        plan_free_device(p);
+        delete p;
+    }
     return nullptr;
 }
 
@@ -227,10 +231,16 @@ int64_t fftc_plan_bytes(fftc_plan plan) {
 
 fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices) {
     if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
-    if (passes) *passes = plan->npasses;
     int cnt = 0;
     int tmp[32];
-    for (int i = 0; i < plan->npasses; ++i) {
+    if (plan->uneven) {
+        if (passes) *passes = 1;
+        HostSched h = host_sched(uneven_max_logn(plan), 4);
+        for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];
+    } else if (passes) {
+        *passes = plan->npasses;
+    }
+    for (int i = 0; i < plan->npasses && !plan->uneven; ++i) {
         const PassPlan &pp = plan->pass[i];
         HostSched h = host_sched(pp.logl, pp.loge);
         for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];
@@ -248,6 +258,28 @@ fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream
     if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
         return FFTC_ERR_MISALIGNED;
     return plan_run(plan, in, out, nullptr, 0.f, (cudaStream_t)stream);
+}
+
+fftc_plan fftc_plan_create_uneven(int64_t count, const int64_t *n, const int8_t *direction, const int64_t *offset,
+                                  fftc_layout layout, fftc_precision precision) {
+    if (count < 1 || count > (int64_t(1) << 24) || !n || !direction || !offset) return fail(FFTC_ERR_INVALID_VALUE);
+    if (layout != FFTC_LAYOUT_INTERLEAVED) return fail(FFTC_ERR_INVALID_VALUE);
+    if (precision != FFTC_FP32) return fail(FFTC_ERR_INVALID_VALUE);
+    for (int64_t i = 0; i < count; ++i)
+        if (n[i] < 64 || n[i] > (int64_t(1) << 16) || !is_pow2(n[i])) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    fftc_plan_s *p = new (std::nothrow) fftc_plan_s();
+    if (!p) return fail(FFTC_ERR_ALLOC);
+    p->magic = FFTC_PLAN_MAGIC;
+    p->layout = layout;
+    p->precision = precision;
+    p->batch = count;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(FFTC_ERR_CUDA, p);
+    fftc_status st = uneven_build(p, count, n, direction, offset);
+    if (st != FFTC_OK) return fail(st, p);
+    p->npasses = 1;
+    register_plan(p);
+    g_last_error = FFTC_OK;
+    return p;
 }
 
 fftc_status fftc_execute_pointwise(fftc_plan plan, const void *in, void *out, const float *h, float scale,

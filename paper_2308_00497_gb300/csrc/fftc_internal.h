@@ -38,6 +38,13 @@ struct PassParams {
     int32_t log_n2;        // log2 N of the inter-pass twiddle (COLS only)
     int32_t tw2_lo_bits;
     int32_t conj_in, conj_out;  // conjugate on load / on store (inverse = conj F conj)
+    // indexed lines (uneven batches): line g starts at complex offset line_off[g] of both
+    // arrays and is conjugated on load and store when line_conj[g] != 0
+    const int64_t *line_off;
+    const int8_t *line_conj;
+    // persistent launches: when set, `in` / `out` hold byte offsets into the launch's
+    // user input / output buffers instead of pointers
+    int32_t in_user, out_user;
 };
 
 typedef cudaError_t (*LaunchFn)(const PassParams &, cudaStream_t);

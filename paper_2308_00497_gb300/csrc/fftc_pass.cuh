@@ -23,7 +23,7 @@
 
 namespace fftc {
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false>
 struct Pass {
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
@@ -55,14 +55,23 @@ struct Pass {
             __syncthreads();
     }
 
-    __device__ __forceinline__ static int64_t line_off(int64_t g, int log_lpt, int64_t tr, int64_t line) {
-        return (g >> log_lpt) * tr + (g & ((int64_t(1) << log_lpt) - 1)) * line;
+    __device__ __forceinline__ static int64_t line_off(const PassParams &p, int64_t g, int64_t tr, int64_t line) {
+        if constexpr (IDX) return __ldg(p.line_off + g);
+        return (g >> p.log_lpt) * tr + (g & ((int64_t(1) << p.log_lpt) - 1)) * line;
     }
+    __device__ __forceinline__ static int conj_of(const PassParams &p, int64_t g, int flag) {
+        if constexpr (IDX) return __ldg(p.line_conj + g);
+        return flag;
+    }
+    // the four-step workspace is written in the same launch in persistent mode: read it
+    // from L2 only, never through a possibly stale L1 line
+    static constexpr bool IN_L2ONLY = (KIND == KIND_ROWST);
 
     template <int R>
     __device__ __forceinline__ static void load_global(const PassParams &p, float2 (&v)[E], int tau, int64_t g,
                                                        bool live) {
-        const int64_t base = line_off(g, p.log_lpt, p.in_tr, p.in_line);
+        const int64_t base = line_off(p, g, p.in_tr, p.in_line);
+        const int cj = conj_of(p, g, p.conj_in);
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
 #pragma unroll
@@ -72,13 +81,14 @@ struct Pass {
                 float2 x = make_float2(0.f, 0.f);
                 if (live) {
                     if constexpr (LIN == LAYOUT_IL) {
-                        x = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
+                        if constexpr (IN_L2ONLY) x = __ldcg(reinterpret_cast<const float2 *>(p.in) + off);
+                        else x = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
                     } else {
                         x.x = __ldcs(p.in + off);
                         x.y = __ldcs(p.in + p.in_plane + off);
                     }
                 }
-                if (p.conj_in) x.y = -x.y;
+                if (cj) x.y = -x.y;
                 v[q * R + t] = x;
             }
         }
@@ -89,7 +99,8 @@ struct Pass {
                                                         bool live) {
         if (!live) return;
         const int64_t l = g & ((int64_t(1) << p.log_lpt) - 1);
-        const int64_t base = line_off(g, p.log_lpt, p.out_tr, p.out_line);
+        const int64_t base = line_off(p, g, p.out_tr, p.out_line);
+        const int cj = conj_of(p, g, p.conj_out);
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
 #pragma unroll
@@ -108,7 +119,7 @@ struct Pass {
                     x.x *= h;
                     x.y *= h;
                 }
-                if (p.conj_out) x.y = -x.y;
+                if (cj) x.y = -x.y;
                 const int64_t off = base + (int64_t)a * p.out_elem;
                 if constexpr (LOUT == LAYOUT_IL) {
                     __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
@@ -170,6 +181,12 @@ struct Pass {
         extern __shared__ float2 sm_dyn[];
         float2 v[E];
         stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
+    }
+
+    // one tile (C lines starting at line tile * C) with the caller's shared memory
+    __device__ __forceinline__ static void run_tile(const PassParams &p, int64_t tile, float2 *sm) {
+        float2 v[E];
+        stage<0>(p, sm, v, threadIdx.x, tile * C);
     }
 };
 

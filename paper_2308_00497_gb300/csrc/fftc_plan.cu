@@ -206,14 +206,20 @@ fftc_status plan_run_tc(fftc_plan_s *p, const void *in, void *out, cudaStream_t 
 
 fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
                      cudaStream_t st) {
-    if (p->uneven) return FFTC_ERR_INVALID_PLAN;  // uneven plans run through fftc_uneven.cu
+    cudaEvent_t *ev = nullptr;
+    if (p->probe_on && p->probe_used < p->probe_slots) ev = &p->probe_events[(size_t)3 * p->probe_used++];
+    if (p->uneven) {
+        if (post_h) return FFTC_ERR_INVALID_VALUE;
+        if (ev) cudaEventRecord(ev[0], st);
+        fftc_status s = uneven_run(p, in, out, st);
+        if (ev) cudaEventRecord(ev[1], st);
+        return s;
+    }
     if (p->precision != FFTC_FP32) {
         if (post_h) return FFTC_ERR_INVALID_VALUE;
         return plan_run_tc(p, in, out, st);
     }
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
-    cudaEvent_t *ev = nullptr;
-    if (p->probe_on && p->probe_used < p->probe_slots) ev = &p->probe_events[(size_t)3 * p->probe_used++];
     if (ev) cudaEventRecord(ev[0], st);
     if (p->npasses == 1) {
         PassParams a = p->pass[0].base;
@@ -244,6 +250,8 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     if (ev) cudaEventRecord(ev[2], st);
     return FFTC_OK;
 }
+
+void plan_destroy_extra(fftc_plan_s *p) { uneven_free(p); }
 
 void plan_probe_free(fftc_plan_s *p) {
     for (cudaEvent_t e : p->probe_events) cudaEventDestroy(e);

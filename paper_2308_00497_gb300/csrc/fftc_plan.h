@@ -67,6 +67,12 @@ cudaError_t plan_upload(fftc_plan_s *p, const void *host, size_t bytes, void **o
 void unit_root(int64_t m, int64_t L, double *cosv, double *sinv);
 void stage_twiddles(int logl, int loge, std::vector<float2> &out);
 
+// uneven batches (fftc_uneven.cu)
+fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir, const int64_t *off);
+fftc_status uneven_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
+void uneven_free(fftc_plan_s *p);
+int uneven_max_logn(const fftc_plan_s *p);
+
 // Kernel choice for a pass; overridable through FFTC_TUNE_* environment variables
 // by the tuner. Returns false if no compiled kernel fits.
 bool choose_rows(int logn, int lin, int *loge, int *lines);

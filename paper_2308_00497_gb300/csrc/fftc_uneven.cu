@@ -1,0 +1,447 @@
+// Uneven batches: many transforms of different power-of-two lengths in ONE persistent
+// kernel launch, replayed from a CUDA graph built when the plan is created.
+//
+// Every transform is cut into CTA tiles of a fused Stockham pass (fftc_pass.cuh):
+//   n <= 2^12 (by default): single-pass tiles; the transforms of one length form a
+//             "class" whose rows are gathered by offset (indexed lines), C rows a tile;
+//   n >= 2^13: the four-step split of Eq. 1 (n = M * K): pass-1 column tiles write a
+//             per-transform workspace, pass-2 row tiles read it back.
+// A work list orders the tiles (pass-1 tiles of the largest transforms first, then the
+// single-pass tiles from large to small, then the pass-2 tiles); CTAs take the next item
+// with one atomic add. A pass-2 tile first waits (bounded spin, thread 0, acquire load)
+// until every pass-1 tile of its transform has signalled completion; pass-1 tiles never
+// wait, and any pass-1 tile a pass-2 tile depends on was taken earlier by a running CTA,
+// so the waits always end. A wait that exceeds its iteration limit sets the plan's error
+// word and the tile proceeds (fftc_plan_check then reports FFTC_ERR_TIMEOUT).
+// All branches run 256-thread CTAs with E <= 16 (3 CTAs per SM).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "../../include/fftc.h"
+#include "fftc_pass.cuh"
+#include "fftc_plan.h"
+
+namespace fftc {
+
+// (id, LOGL, LOGE, C, KIND, IDX): every branch has C * 2^(LOGL - LOGE) = 256 threads
+#define FFTC_UNEVEN_BRANCHES(X)            \
+    X(0, 6, 4, 64, KIND_ROWS, true)        \
+    X(1, 7, 4, 32, KIND_ROWS, true)        \
+    X(2, 8, 4, 16, KIND_ROWS, true)        \
+    X(3, 9, 4, 8, KIND_ROWS, true)         \
+    X(4, 10, 4, 4, KIND_ROWS, true)        \
+    X(5, 11, 4, 2, KIND_ROWS, true)        \
+    X(6, 12, 4, 1, KIND_ROWS, true)        \
+    X(7, 6, 2, 16, KIND_COLS, false)       \
+    X(8, 7, 3, 16, KIND_COLS, false)       \
+    X(9, 8, 4, 16, KIND_COLS, false)       \
+    X(10, 6, 2, 16, KIND_ROWST, false)     \
+    X(11, 7, 3, 16, KIND_ROWST, false)     \
+    X(12, 8, 4, 16, KIND_ROWST, false)
+
+#define FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX) Pass<LOGL, LOGE, C, KIND, LAYOUT_IL, LAYOUT_IL, IDX>
+
+struct BranchInfo {
+    int logl, loge, lines, kind, smem;
+};
+#define FFTC_BRANCH_INFO(ID, LOGL, LOGE, C, KIND, IDX) \
+    BranchInfo{LOGL, LOGE, C, KIND, FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX)::SMEM},
+static const BranchInfo kBranches[] = {FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_INFO)};
+static const int kNumBranches = sizeof(kBranches) / sizeof(kBranches[0]);
+
+#define FFTC_BRANCH_CHECK(ID, LOGL, LOGE, C, KIND, IDX) \
+    static_assert(FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX)::NT == 256, "uneven branches use 256 threads");
+FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_CHECK)
+
+static constexpr int kUnevenThreads = 256;
+
+struct WorkItem {
+    int32_t branch, param, tile;
+    int32_t wait_idx, wait_target;  // wait until done[wait_idx] >= wait_target (-1: none)
+    int32_t signal_idx;             // after the tile: done[signal_idx] += 1 (-1: none)
+};
+
+struct PersArgs {
+    const WorkItem *items;
+    const PassParams *params;
+    unsigned int *ctrl;  // ctrl[0] = next work item, ctrl[1 + i] = done counter i
+    const float *in;
+    float *out;
+    int *err;
+    long long spin_limit;
+    int32_t n_items;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kUnevenThreads, 3) k_uneven(const __grid_constant__ PersArgs a) {
+    extern __shared__ float2 sm_pers[];
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(a.ctrl, 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= a.n_items) break;
+        const WorkItem it = a.items[idx];
+        if (it.wait_idx >= 0) {
+            if (threadIdx.x == 0) {
+                long long spins = 0;
+                while (ld_acquire_gpu(a.ctrl + 1 + it.wait_idx) < (unsigned)it.wait_target) {
+                    if (++spins > a.spin_limit) {
+                        atomicExch(a.err, 1);
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+            __syncthreads();
+        }
+        PassParams p = a.params[it.param];
+        if (p.in_user) p.in = reinterpret_cast<const float *>(reinterpret_cast<const char *>(a.in) + (intptr_t)p.in);
+        if (p.out_user) p.out = reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (intptr_t)p.out);
+        switch (it.branch) {
+#define FFTC_BRANCH_CASE(ID, LOGL, LOGE, C, KIND, IDX) \
+    case ID: FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX)::run_tile(p, it.tile, sm_pers); break;
+            FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_CASE)
+            default: break;
+        }
+        if (it.signal_idx >= 0) {
+            __threadfence();  // this thread's stores are visible device-wide ...
+            __syncthreads();  // ... before thread 0 signals for the whole CTA
+            if (threadIdx.x == 0) atomicAdd(a.ctrl + 1 + it.signal_idx, 1u);
+        }
+        __syncthreads();  // s_idx and shared memory are reused by the next item
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct UnevenState {
+    std::vector<WorkItem> items;
+    std::vector<PassParams> params;
+    WorkItem *d_items = nullptr;
+    PassParams *d_params = nullptr;
+    unsigned int *d_ctrl = nullptr;
+    int n_ctrl = 0;
+    int grid = 0, smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+    PersArgs args{};
+    int max_logn = 0;
+    int64_t total_elems = 0;
+};
+
+static int find_branch(int kind, int logl, int loge, int lines) {
+    for (int i = 0; i < kNumBranches; ++i)
+        if (kBranches[i].kind == kind && kBranches[i].logl == logl && kBranches[i].loge == loge &&
+            kBranches[i].lines == lines)
+            return i;
+    return -1;
+}
+
+// Configuration of one length class: single pass (logm = 0) or four-step (logm > 0).
+struct ClassCfg {
+    int logm = 0;  // four-step split n = 2^logm * 2^(logn - logm); 0 = single pass
+};
+
+static int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return (v && *v) ? atoi(v) : dflt;
+}
+
+static ClassCfg default_class(int logn) {
+    ClassCfg c;
+    char name[64];
+    snprintf(name, sizeof(name), "FFTC_UNEVEN_LOGM_%d", logn);
+    int dflt = logn <= 12 ? 0 : logn / 2;
+    c.logm = env_int(name, dflt);
+    return c;
+}
+
+static int rows_branch(int logn) { return find_branch(KIND_ROWS, logn, 4, 256 >> (logn - 4)); }
+static int cols_branch(int logl) { return find_branch(KIND_COLS, logl, logl - 4, 16); }
+static int rowst_branch(int logl) { return find_branch(KIND_ROWST, logl, logl - 4, 16); }
+
+static bool class_supported(int logn, const ClassCfg &c) {
+    if (c.logm == 0) return rows_branch(logn) >= 0;
+    const int logk = logn - c.logm;
+    return cols_branch(c.logm) >= 0 && rowst_branch(logk) >= 0;
+}
+
+int uneven_max_logn(const fftc_plan_s *p) { return p->uneven ? p->uneven->max_logn : 0; }
+
+void uneven_free(fftc_plan_s *p) {
+    UnevenState *u = p->uneven;
+    if (!u) return;
+    if (u->exec) cudaGraphExecDestroy(u->exec);
+    if (u->graph) cudaGraphDestroy(u->graph);
+    delete u;
+    p->uneven = nullptr;
+}
+
+static cudaError_t build_graph(UnevenState *u, int *d_err, cudaStream_t st) {
+    (void)st;
+    cudaError_t e = cudaGraphCreate(&u->graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t mnode;
+    cudaMemsetParams mp{};
+    mp.dst = u->d_ctrl;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = (size_t)u->n_ctrl;
+    mp.height = 1;
+    mp.pitch = 0;
+    if ((e = cudaGraphAddMemsetNode(&mnode, u->graph, nullptr, 0, &mp)) != cudaSuccess) return e;
+    u->args.items = u->d_items;
+    u->args.params = u->d_params;
+    u->args.ctrl = u->d_ctrl;
+    u->args.err = d_err;
+    u->args.n_items = (int32_t)u->items.size();
+    u->args.in = nullptr;
+    u->args.out = nullptr;
+    void *kargs[] = {&u->args};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)k_uneven;
+    kp.gridDim = dim3(u->grid);
+    kp.blockDim = dim3(kUnevenThreads);
+    kp.sharedMemBytes = u->smem;
+    kp.kernelParams = kargs;
+    if ((e = cudaGraphAddKernelNode(&u->knode, u->graph, &mnode, 1, &kp)) != cudaSuccess) return e;
+    return cudaGraphInstantiate(&u->exec, u->graph, 0);
+}
+
+fftc_status uneven_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st) {
+    UnevenState *u = p->uneven;
+    if (u->args.in != in || u->args.out != out) {
+        u->args.in = (const float *)in;
+        u->args.out = (float *)out;
+        void *kargs[] = {&u->args};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)k_uneven;
+        kp.gridDim = dim3(u->grid);
+        kp.blockDim = dim3(kUnevenThreads);
+        kp.sharedMemBytes = u->smem;
+        kp.kernelParams = kargs;
+        if (cudaGraphExecKernelNodeSetParams(u->exec, u->knode, &kp) != cudaSuccess) return FFTC_ERR_CUDA;
+    }
+    if (cudaGraphLaunch(u->exec, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    return FFTC_OK;
+}
+
+fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir, const int64_t *off) {
+    UnevenState *u = new (std::nothrow) UnevenState();
+    if (!u) return FFTC_ERR_ALLOC;
+    p->uneven = u;
+
+    // validate and find the extent of the buffers
+    std::vector<int64_t> order((size_t)count);
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (n[i] < 64 || n[i] > (int64_t(1) << 16) || (n[i] & (n[i] - 1))) return FFTC_ERR_UNSUPPORTED_SIZE;
+        if (dir[i] != -1 && dir[i] != 1) return FFTC_ERR_INVALID_VALUE;
+        if (off[i] < 0) return FFTC_ERR_INVALID_VALUE;
+        order[(size_t)i] = i;
+        total = std::max(total, off[i] + n[i]);
+    }
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return off[a] < off[b]; });
+    for (size_t k = 1; k < order.size(); ++k)
+        if (off[order[k - 1]] + n[order[k - 1]] > off[order[k]]) return FFTC_ERR_INVALID_VALUE;  // overlap
+    u->total_elems = total;
+    p->total_elems = total;
+
+    // classes by length
+    std::map<int, std::vector<int64_t>> by_log;
+    for (int64_t i = 0; i < count; ++i) {
+        int lg = 0;
+        while ((int64_t(1) << lg) < n[i]) ++lg;
+        by_log[lg].push_back(i);
+        u->max_logn = std::max(u->max_logn, lg);
+    }
+
+    // device tables: stage twiddles per (L, E), inter-pass tables per four-step length
+    std::map<std::pair<int, int>, float2 *> stage_tab;
+    auto stage_table = [&](int logl, int loge, float2 **out) -> fftc_status {
+        auto key = std::make_pair(logl, loge);
+        auto it = stage_tab.find(key);
+        if (it != stage_tab.end()) {
+            *out = it->second;
+            return FFTC_OK;
+        }
+        std::vector<float2> tw;
+        stage_twiddles(logl, loge, tw);
+        void *d = nullptr;
+        if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        stage_tab[key] = (float2 *)d;
+        *out = (float2 *)d;
+        return FFTC_OK;
+    };
+
+    // workspace for the four-step transforms
+    int64_t ws_elems = 0;
+    std::map<int, ClassCfg> cfg;
+    for (auto &kv : by_log) {
+        ClassCfg c = default_class(kv.first);
+        if (!class_supported(kv.first, c)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        cfg[kv.first] = c;
+        if (c.logm) ws_elems += (int64_t(1) << kv.first) * (int64_t)kv.second.size();
+    }
+    void *d = nullptr;
+    float2 *ws = nullptr;
+    if (ws_elems) {
+        if (plan_alloc(p, (size_t)ws_elems * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        ws = (float2 *)d;
+    }
+
+    // work items: pass-1 tiles (largest first), single-pass tiles (largest first), pass-2 tiles
+    std::vector<WorkItem> p1, p0, p2;
+    int n_done = 0;
+    int64_t ws_off = 0;
+    for (auto it = by_log.rbegin(); it != by_log.rend(); ++it) {
+        const int logn = it->first;
+        const std::vector<int64_t> &ids = it->second;
+        const ClassCfg &c = cfg[logn];
+        const int64_t nn = int64_t(1) << logn;
+        if (c.logm == 0) {
+            const int b = rows_branch(logn);
+            const BranchInfo &bi = kBranches[b];
+            std::vector<int64_t> loff(ids.size());
+            std::vector<int8_t> lconj(ids.size());
+            for (size_t k = 0; k < ids.size(); ++k) {
+                loff[k] = off[ids[k]];
+                lconj[k] = dir[ids[k]] == 1 ? 1 : 0;
+            }
+            if (plan_upload(p, loff.data(), loff.size() * sizeof(int64_t), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+            const int64_t *d_off = (const int64_t *)d;
+            if (plan_upload(p, lconj.data(), lconj.size(), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+            const int8_t *d_conj = (const int8_t *)d;
+            PassParams q{};
+            float2 *tw = nullptr;
+            fftc_status s = stage_table(logn, bi.loge, &tw);
+            if (s != FFTC_OK) return s;
+            q.tw = tw;
+            q.total_lines = (int64_t)ids.size();
+            q.in_elem = q.out_elem = 1;
+            q.line_off = d_off;
+            q.line_conj = d_conj;
+            q.in_user = q.out_user = 1;
+            q.in = nullptr;  // byte offset 0 into the user buffers
+            q.out = nullptr;
+            const int pi = (int)u->params.size();
+            u->params.push_back(q);
+            const int64_t tiles = ((int64_t)ids.size() + bi.lines - 1) / bi.lines;
+            for (int64_t t = 0; t < tiles; ++t) p0.push_back(WorkItem{b, pi, (int32_t)t, -1, 0, -1});
+        } else {
+            const int logm = c.logm, logk = logn - logm;
+            const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
+            const int b1 = cols_branch(logm), b2 = rowst_branch(logk);
+            float2 *tw1 = nullptr, *tw2 = nullptr;
+            fftc_status s = stage_table(logm, kBranches[b1].loge, &tw1);
+            if (s != FFTC_OK) return s;
+            if ((s = stage_table(logk, kBranches[b2].loge, &tw2)) != FFTC_OK) return s;
+            // inter-pass tables of this length
+            const int lob = (logn + 1) / 2;
+            const int64_t nlo = int64_t(1) << lob, nhi = nn >> lob;
+            std::vector<float2> lo(nlo), hi(nhi);
+            for (int64_t m = 0; m < nlo; ++m) {
+                double cc, ss;
+                unit_root(m, nn, &cc, &ss);
+                lo[m] = make_float2((float)cc, (float)-ss);
+            }
+            for (int64_t m = 0; m < nhi; ++m) {
+                double cc, ss;
+                unit_root(m * nlo, nn, &cc, &ss);
+                hi[m] = make_float2((float)cc, (float)-ss);
+            }
+            if (plan_upload(p, lo.data(), lo.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+            const float2 *d_lo = (const float2 *)d;
+            if (plan_upload(p, hi.data(), hi.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+            const float2 *d_hi = (const float2 *)d;
+            for (int64_t id : ids) {
+                const int conj = dir[id] == 1 ? 1 : 0;
+                PassParams a{};
+                a.in_user = 1;
+                a.in = reinterpret_cast<const float *>((intptr_t)(off[id] * 8));
+                a.out = reinterpret_cast<float *>(ws + ws_off);
+                a.total_lines = K;
+                a.log_lpt = logk;
+                a.in_tr = a.out_tr = nn;
+                a.in_line = a.out_line = 1;
+                a.in_elem = a.out_elem = K;
+                a.tw = tw1;
+                a.tw2_lo = d_lo;
+                a.tw2_hi = d_hi;
+                a.log_n2 = logn;
+                a.tw2_lo_bits = lob;
+                a.conj_in = conj;
+                PassParams b{};
+                b.in = reinterpret_cast<const float *>(ws + ws_off);
+                b.out_user = 1;
+                b.out = reinterpret_cast<float *>((intptr_t)(off[id] * 8));
+                b.total_lines = M;
+                b.log_lpt = logm;
+                b.in_tr = b.out_tr = nn;
+                b.in_line = K;
+                b.in_elem = 1;
+                b.out_line = 1;
+                b.out_elem = M;
+                b.tw = tw2;
+                b.conj_out = conj;
+                const int pa = (int)u->params.size();
+                u->params.push_back(a);
+                const int pb = (int)u->params.size();
+                u->params.push_back(b);
+                const int done = n_done++;
+                const int64_t t1 = K / 16, t2 = M / 16;
+                for (int64_t t = 0; t < t1; ++t) p1.push_back(WorkItem{b1, pa, (int32_t)t, -1, 0, done});
+                for (int64_t t = 0; t < t2; ++t) p2.push_back(WorkItem{b2, pb, (int32_t)t, done, (int32_t)t1, -1});
+                ws_off += nn;
+            }
+        }
+    }
+    if (env_int("FFTC_TEST_UNREACHABLE_WAIT", 0))  // test hook: a dependency nothing satisfies
+        for (WorkItem &w : p2) w.wait_target += 1;
+    u->items = p1;
+    u->items.insert(u->items.end(), p0.begin(), p0.end());
+    u->items.insert(u->items.end(), p2.begin(), p2.end());
+    u->n_ctrl = 1 + n_done;
+
+    if (plan_upload(p, u->items.data(), u->items.size() * sizeof(WorkItem), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    u->d_items = (WorkItem *)d;
+    if (plan_upload(p, u->params.data(), u->params.size() * sizeof(PassParams), &d) != cudaSuccess)
+        return FFTC_ERR_ALLOC;
+    u->d_params = (PassParams *)d;
+    if (plan_alloc(p, (size_t)u->n_ctrl * sizeof(unsigned int), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    u->d_ctrl = (unsigned int *)d;
+    if (plan_alloc(p, 16, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->d_err = (int *)d;
+    if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
+
+    // launch shape: every SM full of resident CTAs
+    int smem = 0;
+    for (int i = 0; i < kNumBranches; ++i) smem = std::max(smem, kBranches[i].smem);
+    u->smem = smem;
+    if (cudaFuncSetAttribute(k_uneven, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return FFTC_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uneven, kUnevenThreads, smem) != cudaSuccess)
+        return FFTC_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return FFTC_ERR_CUDA;
+    u->grid = std::max(1, per_sm) * sms;
+    u->args.spin_limit = (long long)env_int("FFTC_SPIN_LIMIT", 20000000);
+    if (build_graph(u, p->d_err, nullptr) != cudaSuccess) return FFTC_ERR_CUDA;
+    return FFTC_OK;
+}
+
+}  // namespace fftc

@@ -75,3 +75,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(nat, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         nat.load()
+
+
+def test_uneven_validation_before_any_device_call(lib):
+    import numpy as np
+    from paper_2308_00497_gb300 import _native as nat
+    n = np.array([64, 32], dtype=np.int64)
+    d = np.array([-1, 1], dtype=np.int8)
+    o = np.array([0, 64], dtype=np.int64)
+    assert not lib.fftc_plan_create_uneven(2, n.ctypes.data, d.ctypes.data, o.ctypes.data, 0, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE       # 32 < 64
+    assert not lib.fftc_plan_create_uneven(0, n.ctypes.data, d.ctypes.data, o.ctypes.data, 0, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE
+    assert not lib.fftc_plan_create_uneven(1, n.ctypes.data, d.ctypes.data, o.ctypes.data, 1, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE          # split layout

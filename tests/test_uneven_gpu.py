@@ -1,0 +1,113 @@
+"""Uneven batches in one persistent launch (graph replay): parity with the oracle,
+determinism, buffer switching, and the bounded-wait error path (made to time out on
+purpose with a dependency nothing satisfies; the GPU context stays usable)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic_inputs as si
+from gpu_util import rel_l2_rows, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2308_00497_gb300 import build
+    build.build()
+
+
+def _check_rows(x, y, n, d, o, rows):
+    for i in rows:
+        xi = x[o[i]:o[i] + n[i]].astype(np.complex128)
+        ref = oracle.fft(xi, inverse=d[i] == 1)
+        err = rel_l2_rows(y[o[i]:o[i] + n[i]][None], ref[None])[0]
+        assert err <= tol_fp32(int(n[i])), (i, int(n[i]), float(err))
+
+
+def test_small_uneven_batch_all_rows():
+    import paper_2308_00497_gb300 as fc
+    rng = np.random.default_rng(3)
+    e = np.concatenate([np.arange(6, 17), rng.integers(6, 17, 29)])
+    n = (1 << e).astype(np.int64)
+    d = np.where(rng.random(n.size) < 0.5, -1, 1).astype(np.int8)
+    gaps = rng.integers(0, 3, n.size) * 16          # rows need not be packed
+    o = np.concatenate([[0], np.cumsum(n + gaps)[:-1]]).astype(np.int64)
+    total = int(o[-1] + n[-1])
+    x = si.uniform_complex(1, total, seed=9).reshape(total)
+    p = fc.UnevenPlan(n, d, o)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    p.execute(xd, yd)
+    torch.cuda.synchronize()
+    p.check()
+    _check_rows(x, yd.cpu().numpy(), n, d, o, range(n.size))
+
+
+def test_workload_4096_sampled_and_deterministic():
+    import paper_2308_00497_gb300 as fc
+    n, d, o, total = si.uneven_batch(4096, seed=4)
+    x = si.uneven_data(total, seed=4)
+    p = fc.UnevenPlan(n, d, o)
+    xd = torch.from_numpy(x).cuda()
+    y1 = torch.empty_like(xd)
+    p.execute(xd, y1)
+    y2 = p.execute(xd)              # another output buffer: the graph's node is updated
+    y3 = torch.empty_like(xd)
+    p.execute(xd, y3)
+    torch.cuda.synchronize()
+    p.check()
+    assert torch.equal(y1.view(torch.float32), y2.view(torch.float32))
+    assert torch.equal(y1.view(torch.float32), y3.view(torch.float32))
+    rng = np.random.default_rng(1)
+    rows = []
+    for lg in range(6, 17):        # three rows of every length, both directions present
+        idx = np.flatnonzero(n == (1 << lg))
+        rows += list(rng.choice(idx, size=min(3, idx.size), replace=False))
+    _check_rows(x, y1.cpu().numpy(), n, d, o, rows)
+
+
+def test_in_place_uneven():
+    import paper_2308_00497_gb300 as fc
+    n, d, o, total = si.uneven_batch(200, seed=5)
+    x = si.uneven_data(total, seed=5)
+    p = fc.UnevenPlan(n, d, o)
+    xd = torch.from_numpy(x).cuda()
+    p.execute(xd, xd)
+    torch.cuda.synchronize()
+    _check_rows(x, xd.cpu().numpy(), n, d, o, range(0, 200, 7))
+
+
+def test_bounded_wait_reports_timeout(monkeypatch):
+    """Pass-2 tiles wait for a count nothing reaches; with a tiny spin limit every wait
+    gives up, the kernel returns, and fftc_plan_check reports FFTC_ERR_TIMEOUT."""
+    import paper_2308_00497_gb300 as fc
+    from paper_2308_00497_gb300 import _native as nat
+    monkeypatch.setenv("FFTC_TEST_UNREACHABLE_WAIT", "1")
+    monkeypatch.setenv("FFTC_SPIN_LIMIT", "200")
+    n = np.array([1 << 14, 1 << 13, 256], dtype=np.int64)
+    d = np.array([-1, 1, -1], dtype=np.int8)
+    o = np.array([0, 1 << 14, 3 << 13], dtype=np.int64)
+    p = fc.UnevenPlan(n, d, o)
+    x = torch.zeros(int(o[-1] + n[-1]), dtype=torch.complex64, device="cuda")
+    p.execute(x)
+    with pytest.raises(nat.FftcError) as ei:
+        p.check()
+    assert ei.value.status == nat.ERR_TIMEOUT
+    p.check()  # the error word was cleared
+    monkeypatch.delenv("FFTC_TEST_UNREACHABLE_WAIT")
+    monkeypatch.delenv("FFTC_SPIN_LIMIT")
+    q = fc.UnevenPlan(n, d, o)  # the context is still usable
+    y = q.execute(torch.ones_like(x))
+    torch.cuda.synchronize()
+    q.check()
+    assert torch.isfinite(y.view(torch.float32)).all()
+
+
+def test_uneven_rejects_bad_descriptors():
+    import paper_2308_00497_gb300 as fc
+    from paper_2308_00497_gb300 import _native as nat
+    with pytest.raises(nat.FftcError) as ei:   # overlapping rows
+        fc.UnevenPlan(np.array([64, 64]), np.array([-1, -1]), np.array([0, 32]))
+    assert ei.value.status == nat.ERR_INVALID_VALUE
