@@ -267,6 +267,8 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
                "h2d_bytes_per_step": 8 * ELEMS * len(plans), "d2h_bytes_per_step": 8 * ELEMS * len(plans),
                "steps": args.e2e_steps}
 
+    extras = {} if args.no_extras else run_extras(args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = 0
@@ -295,10 +297,82 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
             "clocks": clk,
             "gpu_launches": launches,
             "per_size": per_size,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _time_ms(fn, reps: int) -> float:
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_extras(args, dev) -> dict:
+    """Secondary workloads, each against the plain FP32 form on the same GPU."""
+    import numpy as np
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    import synthetic_inputs as si
+    from paper_2308_00497_gb300.autograd import spectral_filter
+    out = {}
+    reps = max(3, args.steps)
+
+    # uneven batch: 4096 rows, n = 2^6..2^16 log-uniform, mixed directions, one launch
+    n, d, o, total = si.uneven_batch(4096, seed=4)
+    x = torch.from_numpy(si.uneven_data(total, seed=4)).to(dev)
+    y = torch.empty_like(x)
+    up = fc.UnevenPlan(n, d, o, device=dev)
+    t_uneven = _time_ms(lambda: up.execute(x, y), reps)
+    fl = sum(5.0 * int(v) * math.log2(int(v)) for v in n)
+    # the same rows as one uniform batched plan per (n, direction) class, separate launches
+    classes = {}
+    for v, dd in zip(n.tolist(), d.tolist()):
+        classes[(v, dd)] = classes.get((v, dd), 0) + 1
+    bufs, plans = [], []
+    for (v, dd), cnt in classes.items():
+        xb = torch.zeros((cnt, v), dtype=torch.complex64, device=dev)
+        bufs.append((xb, torch.empty_like(xb)))
+        plans.append(fc.Plan(v, cnt, "interleaved", dd == 1, device=dev))
+    def per_class():
+        for (xb, yb), p in zip(bufs, plans):
+            p.execute(xb, yb)
+    t_sep = _time_ms(per_class, reps)
+    out["uneven"] = {"workload": "4096 rows, n=2^6..2^16 log-uniform, mixed fwd/inv, interleaved, one persistent "
+                                 "launch from a CUDA graph", "elements": int(total), "ms": round(t_uneven, 4),
+                     "gflops": round(fl / (t_uneven * 1e-3) / 1e9, 1),
+                     "hbm_frac_strict": round(16.0 * total / (t_uneven * 1e-3) / 1e9 / peaks()[0], 4),
+                     "separate_launches_ms": round(t_sep, 4), "separate_launches": len(plans),
+                     "speedup_vs_separate": round(t_sep / t_uneven, 3)}
+    del bufs, plans, x, y
+
+    # differentiation: batched spectral filter forward + backward, [1024, 2^14]
+    B, nn = 1024, 1 << 14
+    xs = torch.from_numpy(si.gaussian_complex(B, nn, seed=5)).to(dev).requires_grad_(True)
+    ts = torch.from_numpy(si.gaussian_complex(B, nn, seed=55)).to(dev)
+    H = torch.from_numpy(si.gaussian_lowpass(nn)).to(dev)
+    def fwd_bwd():
+        xs.grad = None
+        yv = spectral_filter(xs, H)
+        yv.backward(2.0 * (yv.detach() - ts))   # dL/dy of ||y - t||^2
+    t_fb = _time_ms(fwd_bwd, reps)
+    fp = fc.get_plan(nn, B, "interleaved", False, device=dev)
+    xf = xs.detach().clone()
+    t_fft = _time_ms(lambda: fp.execute(xf, xf), reps)
+    out["spectral_filter"] = {"workload": "y = ifft(H * fft(x)) / n, loss ||y - t||^2, x,t [1024, 2^14] complex64",
+                              "fwd_bwd_ms": round(t_fb, 4), "fft_ms": round(t_fft, 4),
+                              "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
+    return out
 
 
 def main():
@@ -310,6 +384,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the uneven / filter / precision lines")
     ap.add_argument("--sizes", default=",".join(str(e) for e in SIZES),
                     help="log2 n list (default: the whole sweep); a subset is for profiling only")
     ap.add_argument("--layouts", default=",".join(LAYOUTS))

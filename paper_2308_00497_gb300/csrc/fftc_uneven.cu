@@ -21,6 +21,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/fftc.h"
@@ -161,14 +163,6 @@ static int env_int(const char *name, int dflt) {
     return (v && *v) ? atoi(v) : dflt;
 }
 
-static ClassCfg default_class(int logn) {
-    ClassCfg c;
-    char name[64];
-    snprintf(name, sizeof(name), "FFTC_UNEVEN_LOGM_%d", logn);
-    int dflt = logn <= 12 ? 0 : logn / 2;
-    c.logm = env_int(name, dflt);
-    return c;
-}
 
 static int rows_branch(int logn) { return find_branch(KIND_ROWS, logn, 4, 256 >> (logn - 4)); }
 static int cols_branch(int logl) { return find_branch(KIND_COLS, logl, logl - 4, 16); }
@@ -240,7 +234,10 @@ fftc_status uneven_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t s
     return FFTC_OK;
 }
 
-fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir, const int64_t *off) {
+typedef int (*ClassChoice)(int logn, void *ctx);
+
+static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir,
+                               const int64_t *off, ClassChoice choose, void *ctx) {
     UnevenState *u = new (std::nothrow) UnevenState();
     if (!u) return FFTC_ERR_ALLOC;
     p->uneven = u;
@@ -292,7 +289,8 @@ fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const 
     int64_t ws_elems = 0;
     std::map<int, ClassCfg> cfg;
     for (auto &kv : by_log) {
-        ClassCfg c = default_class(kv.first);
+        ClassCfg c;
+        c.logm = choose(kv.first, ctx);
         if (!class_supported(kv.first, c)) return FFTC_ERR_UNSUPPORTED_SIZE;
         cfg[kv.first] = c;
         if (c.logm) ws_elems += (int64_t(1) << kv.first) * (int64_t)kv.second.size();
@@ -443,5 +441,151 @@ fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const 
     if (build_graph(u, p->d_err, nullptr) != cudaSuccess) return FFTC_ERR_CUDA;
     return FFTC_OK;
 }
+
+
+// ---------------------------------------------------------------------------
+// autotuner: per length class, time each candidate factorisation inside the
+// persistent kernel and keep the fastest (cached per device; FFTC_TUNE_CACHE names
+// an optional file that carries the choices across processes)
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::pair<std::string, int>, int> g_tuned;  // (device name, log n) -> log m
+static bool g_tune_file_read = false;
+
+static std::vector<int> candidates(int logn) {
+    std::vector<int> c;
+    for (int logm = 0; logm <= 8; ++logm) {
+        if (logm > 0 && logm < 6) continue;
+        ClassCfg cc;
+        cc.logm = logm;
+        if (logm == 0 || (logn - logm >= 6 && logn - logm <= 8)) {
+            if (class_supported(logn, cc)) c.push_back(logm);
+        }
+    }
+    return c;
+}
+
+static int fixed_choice(int logn, void *ctx) {
+    (void)logn;
+    return *static_cast<int *>(ctx);
+}
+
+// Time one candidate: `rows` contiguous rows of length 2^logn, forward, 64 MiB in.
+static double time_candidate(int device, int logn, int logm, void *d_in, void *d_out, int64_t rows) {
+    fftc_plan_s tp;
+    tp.magic = FFTC_PLAN_MAGIC;
+    tp.device = device;
+    std::vector<int64_t> n((size_t)rows, int64_t(1) << logn), off((size_t)rows);
+    std::vector<int8_t> dir((size_t)rows, -1);
+    for (int64_t i = 0; i < rows; ++i) off[(size_t)i] = i << logn;
+    int choice = logm;
+    double best = -1.0;
+    if (build_state(&tp, rows, n.data(), dir.data(), off.data(), fixed_choice, &choice) == FFTC_OK) {
+        cudaStream_t st;
+        cudaEvent_t e0, e1;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            bool ok = uneven_run(&tp, d_in, d_out, st) == FFTC_OK;  // warm-up
+            for (int rep = 0; ok && rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                ok = uneven_run(&tp, d_in, d_out, st) == FFTC_OK;
+                cudaEventRecord(e1, st);
+                float ms = 0.f;
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    best = (best < 0 || ms < best) ? ms : best;
+                else
+                    ok = false;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaStreamDestroy(st);
+        }
+    }
+    uneven_free(&tp);
+    plan_free_device(&tp);
+    return best;
+}
+
+static void read_tune_file(const std::string &dev) {
+    const char *path = getenv("FFTC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char name[256];
+    int logn, logm;
+    while (fscanf(f, " uneven %255[^|]|%d %d", name, &logn, &logm) == 3)
+        if (dev == name) g_tuned[std::make_pair(dev, logn)] = logm;
+    fclose(f);
+}
+
+static void append_tune_file(const std::string &dev, int logn, int logm) {
+    const char *path = getenv("FFTC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "uneven %s|%d %d\n", dev.c_str(), logn, logm);
+    fclose(f);
+}
+
+struct TuneCtx {
+    int device;
+    std::string dev_name;
+    void *d_in, *d_out;
+    int64_t elems;
+};
+
+static int tuned_choice(int logn, void *vctx) {
+    TuneCtx *ctx = static_cast<TuneCtx *>(vctx);
+    char name[64];
+    snprintf(name, sizeof(name), "FFTC_UNEVEN_LOGM_%d", logn);
+    const int forced = env_int(name, -1);
+    if (forced >= 0) return forced;
+    std::vector<int> cand = candidates(logn);
+    if (cand.empty()) return -1;
+    const int dflt = logn <= 12 ? 0 : logn / 2;
+    if (cand.size() == 1 || env_int("FFTC_TUNE", 1) == 0) return dflt;
+    auto key = std::make_pair(ctx->dev_name, logn);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+    if (!ctx->d_in) {  // tuning buffers, freed when the plan is built
+        if (cudaMalloc(&ctx->d_in, (size_t)ctx->elems * 8) != cudaSuccess) ctx->d_in = nullptr;
+        if (ctx->d_in && cudaMalloc(&ctx->d_out, (size_t)ctx->elems * 8) != cudaSuccess) ctx->d_out = nullptr;
+        if (!ctx->d_in || !ctx->d_out) return dflt;
+        cudaMemset(ctx->d_in, 0, (size_t)ctx->elems * 8);
+    }
+    const int64_t rows = ctx->elems >> logn;
+    int best = dflt;
+    double best_ms = -1.0;
+    for (int c : cand) {
+        const double ms = time_candidate(ctx->device, logn, c, ctx->d_in, ctx->d_out, rows);
+        if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    g_tuned[key] = best;
+    append_tune_file(ctx->dev_name, logn, best);
+    return best;
+}
+
+fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir, const int64_t *off) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneCtx ctx{};
+    ctx.device = p->device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return FFTC_ERR_CUDA;
+    ctx.dev_name = prop.name;
+    ctx.elems = int64_t(1) << 23;  // 64 MiB per tuning buffer
+    if (!g_tune_file_read) {
+        read_tune_file(ctx.dev_name);
+        g_tune_file_read = true;
+    }
+    fftc_status s = build_state(p, count, n, dir, off, tuned_choice, &ctx);
+    if (ctx.d_in) cudaFree(ctx.d_in);
+    if (ctx.d_out) cudaFree(ctx.d_out);
+    return s;
+}
+
 
 }  // namespace fftc
