@@ -372,7 +372,45 @@ def run_extras(args, dev) -> dict:
     out["spectral_filter"] = {"workload": "y = ifft(H * fft(x)) / n, loss ||y - t||^2, x,t [1024, 2^14] complex64",
                               "fwd_bwd_ms": round(t_fb, 4), "fft_ms": round(t_fft, 4),
                               "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
+    del xs, ts, xf
+    if not args.no_precision:
+        out["precision"] = run_precision(args, dev, reps)
     return out
+
+
+def run_precision(args, dev, reps: int) -> dict:
+    """Radix-16 stages on the tensor cores (FP16/BF16, plain and hi+lo split) vs FP32:
+    n = 2^12..2^16, batch 2^14, complex N(0,1); error on sampled rows vs the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2308_00497_gb300 as fc
+    import synthetic_inputs as si
+    B = 1 << 14
+    full = si.gaussian_complex(1, B << 16, seed=3).reshape(B << 16)   # viewed as [B, n] for every n
+    x_all = torch.from_numpy(full).to(dev)
+    rows = np.array([0, B // 2, B - 1])
+    modes = ["fp32", "fp16_tc", "bf16_tc", "fp16_tc_split", "bf16_tc_split"]
+    res = []
+    for e in range(12, 17):
+        n = 1 << e
+        x = x_all[: n * B].view(B, n)
+        y = torch.empty_like(x)
+        ref = oracle.fft(full[: n * B].reshape(B, n)[rows].astype(np.complex128))
+        for m in modes:
+            p = fc.Plan(n, B, "interleaved", False, m, device=dev)
+            t = _time_ms(lambda: p.execute(x, y), reps)
+            got = y[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.complex128)
+            err = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+            passes, _ = p.info()
+            res.append({"n": n, "mode": m, "ms": round(t, 4), "gflops": round(flops(n, B) / (t * 1e-3) / 1e9, 1),
+                        "hbm_frac_per_pass": round(16.0 * n * B * passes / (t * 1e-3) / 1e9 / peaks()[0], 4),
+                        "rel_l2_max": err})
+            p.close()
+        del x, y
+    return {"workload": "n=2^12..2^16, batch=2^14, complex N(0,1), interleaved, forward", "rows_checked": 3,
+            "results": res}
 
 
 def main():
@@ -385,6 +423,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the uneven / filter / precision lines")
+    ap.add_argument("--no-precision", action="store_true", help="skip the tensor-core precision line")
     ap.add_argument("--sizes", default=",".join(str(e) for e in SIZES),
                     help="log2 n list (default: the whole sweep); a subset is for profiling only")
     ap.add_argument("--layouts", default=",".join(LAYOUTS))

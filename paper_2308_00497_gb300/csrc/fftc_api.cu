@@ -38,11 +38,11 @@ HostSched host_sched(int logl, int loge) {
     return h;
 }
 
-const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout) {
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec) {
     for (int i = 0; i < kernel_count(); ++i) {
         const KernelEntry *e = kernel_at(i);
         if (e->kind == kind && e->logl == logl && e->loge == loge && e->lines == lines && e->lin == lin &&
-            e->lout == lout)
+            e->lout == lout && e->prec == prec)
             return e;
     }
     return nullptr;

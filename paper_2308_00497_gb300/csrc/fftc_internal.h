@@ -56,10 +56,11 @@ struct KernelEntry {
     int smem_bytes;
     LaunchFn launch;
     PrepareFn prepare;
+    int prec;  // fftc_precision of the radix stages (0 = FP32 on CUDA cores)
 };
 
 // Registry of compiled pass kernels (one table per instantiation unit).
-const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout);
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec = 0);
 int kernel_count();
 const KernelEntry *kernel_at(int i);
 

@@ -218,7 +218,7 @@ template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
 constexpr KernelEntry entry() {
     using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
     return KernelEntry{KIND, LOGL, LOGE, C, LIN, LOUT, P::NT, P::SMEM,
-                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT>};
+                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, 0};
 }
 
 }  // namespace fftc

@@ -75,7 +75,10 @@ static fftc_status prepare(PassPlan &pp) {
     return FFTC_OK;
 }
 
-fftc_status plan_build_fp32(fftc_plan_s *p) {
+fftc_status plan_build_passes(fftc_plan_s *p) {
+    const int prec = (int)p->precision;
+    const bool tc = prec != FFTC_FP32;
+    if (tc && (p->logn < 7 || p->logn > 16)) return FFTC_ERR_UNSUPPORTED_SIZE;
     const int64_t n = p->n, B = p->batch;
     const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
     const int64_t plane = (lay == LAYOUT_SPLIT) ? n * B : 0;
@@ -85,14 +88,19 @@ fftc_status plan_build_fp32(fftc_plan_s *p) {
     p->d_err = (int *)d;
     if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
 
-    if (p->logn <= env_int("FFTC_TUNE_MAX_SINGLE_LOG", kMaxSinglePassLog)) {
+    if (p->logn <= (tc ? 13 : env_int("FFTC_TUNE_MAX_SINGLE_LOG", kMaxSinglePassLog))) {
         PassPlan &pp = p->pass[0];
         p->npasses = 1;
         pp.kind = KIND_ROWS;
         pp.logl = p->logn;
-        if (!choose_rows(p->logn, lay, &pp.loge, &pp.lines)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        if (tc) {
+            pp.loge = 4;
+            pp.lines = p->logn >= 12 ? 1 : (4096 >> p->logn);
+        } else if (!choose_rows(p->logn, lay, &pp.loge, &pp.lines)) {
+            return FFTC_ERR_UNSUPPORTED_SIZE;
+        }
         pp.lin = pp.lout = lay;
-        pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay);
+        pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay, prec);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.in_plane = b.out_plane = plane;
@@ -110,7 +118,12 @@ fftc_status plan_build_fp32(fftc_plan_s *p) {
 
     // four-step: n = M * K
     int logm, e1, e2;
-    if (!choose_four_step(p->logn, &logm, &e1, &e2)) return FFTC_ERR_UNSUPPORTED_SIZE;
+    if (tc) {
+        logm = p->logn / 2;
+        e1 = e2 = 4;
+    } else if (!choose_four_step(p->logn, &logm, &e1, &e2)) {
+        return FFTC_ERR_UNSUPPORTED_SIZE;
+    }
     const int logk = p->logn - logm;
     const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
     p->npasses = 2;
@@ -144,7 +157,7 @@ fftc_status plan_build_fp32(fftc_plan_s *p) {
         pp.lines = kPassLines;
         pp.lin = lay;
         pp.lout = LAYOUT_IL;
-        pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout);
+        pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.in_plane = plane;
@@ -173,7 +186,7 @@ fftc_status plan_build_fp32(fftc_plan_s *p) {
         pp.lines = kPassLines;
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
-        pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout);
+        pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.in_plane = 0;
@@ -195,14 +208,7 @@ fftc_status plan_build_fp32(fftc_plan_s *p) {
     return FFTC_OK;
 }
 
-fftc_status plan_build_tc(fftc_plan_s *p);  // fftc_tc.cu
-
-fftc_status plan_build(fftc_plan_s *p) {
-    if (p->precision == FFTC_FP32) return plan_build_fp32(p);
-    return plan_build_tc(p);
-}
-
-fftc_status plan_run_tc(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);  // fftc_tc.cu
+fftc_status plan_build(fftc_plan_s *p) { return plan_build_passes(p); }
 
 fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
                      cudaStream_t st) {
@@ -215,10 +221,7 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
         if (ev) cudaEventRecord(ev[1], st);
         return s;
     }
-    if (p->precision != FFTC_FP32) {
-        if (post_h) return FFTC_ERR_INVALID_VALUE;
-        return plan_run_tc(p, in, out, st);
-    }
+    if (p->precision != FFTC_FP32 && post_h) return FFTC_ERR_INVALID_VALUE;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
     if (ev) cudaEventRecord(ev[0], st);
     if (p->npasses == 1) {

@@ -3,8 +3,9 @@
 
 namespace fftc {
 
-extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[];
-extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount;
+extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
+    kTcBf16Table[];
+extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count;
 
 struct TableRef {
     const KernelEntry *t;
@@ -13,6 +14,7 @@ struct TableRef {
 static const TableRef kTables[] = {
     {kRowsIlTable, &kRowsIlCount}, {kRowsSplitTable, &kRowsSplitCount},
     {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
+    {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
 };
 
 int kernel_count() {

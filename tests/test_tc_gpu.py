@@ -1,0 +1,106 @@
+"""Tensor-core radix-16 precisions against the FP64 oracle.
+
+The paper evaluates FP64 only, so these bounds are derived here from the unit roundoff u
+of each operand format and frozen: a radix-16 stage rounds its inputs and W16 once each,
+so the relative L2 error after s tensor-core stages stays below 2 (s + 1) u, plus the
+FP32 bound of the rest of the path (twiddles, leftover radix, accumulation):
+
+    FP16 plain  u = 2^-11     BF16 plain  u = 2^-8
+    FP16 split  u = 2^-22     BF16 split  u = 2^-16   (hi + lo carry twice the bits)
+
+Inputs are complex Gaussian N(0, 1) (the precision workload). The split modes must also
+beat their plain counterparts by a wide margin.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic_inputs as si
+from gpu_util import from_device, rel_l2_rows, to_device, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+U = {"fp16_tc": 2.0 ** -11, "bf16_tc": 2.0 ** -8, "fp16_tc_split": 2.0 ** -22, "bf16_tc_split": 2.0 ** -16}
+
+
+def bound(mode: str, n: int) -> float:
+    s_tc = int(math.log2(n)) // 4
+    return 2 * (s_tc + 1) * U[mode] + tol_fp32(n)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2308_00497_gb300 import build
+    build.build()
+
+
+def _run(x, layout, inverse, mode):
+    import paper_2308_00497_gb300 as fc
+    t = to_device(x, layout)
+    y = fc.ifft(t, layout=layout, precision=mode) if inverse else fc.fft(t, layout=layout, precision=mode)
+    torch.cuda.synchronize()
+    return from_device(y, layout)
+
+
+SIZES = [7, 8, 10, 11, 12, 13, 14, 15, 16]
+
+
+@pytest.mark.parametrize("mode", list(U))
+@pytest.mark.parametrize("e", SIZES)
+def test_tc_modes_within_bound(mode, e):
+    n = 1 << e
+    B = 37 if n <= 4096 else 5
+    x = si.gaussian_complex(B, n, seed=300 + e)
+    ref = oracle.fft(x.astype(np.complex128))
+    err = rel_l2_rows(_run(x, "interleaved", False, mode), ref).max()
+    assert err <= bound(mode, n), (mode, n, float(err), bound(mode, n))
+
+
+@pytest.mark.parametrize("mode", ["fp16_tc_split", "bf16_tc"])
+@pytest.mark.parametrize("e", [9, 14])
+def test_tc_split_layout_and_inverse(mode, e):
+    n = 1 << e
+    x = si.gaussian_complex(6, n, seed=400 + e)
+    ref = oracle.fft(x.astype(np.complex128), inverse=True)
+    err = rel_l2_rows(_run(x, "split", True, mode), ref).max()
+    assert err <= bound(mode, n), (mode, n, float(err))
+
+
+@pytest.mark.parametrize("e", [8, 12, 16])
+def test_split_recovers_accuracy(e):
+    n = 1 << e
+    x = si.gaussian_complex(8, n, seed=500 + e)
+    ref = oracle.fft(x.astype(np.complex128))
+    err = {m: rel_l2_rows(_run(x, "interleaved", False, m), ref).max() for m in U}
+    assert err["fp16_tc_split"] < err["fp16_tc"] / 50
+    assert err["bf16_tc_split"] < err["bf16_tc"] / 20
+    assert err["bf16_tc"] > err["fp16_tc"]  # fewer mantissa bits, larger error
+
+
+def test_tc_determinism_and_rejects_small_n():
+    import paper_2308_00497_gb300 as fc
+    from paper_2308_00497_gb300 import _native as nat
+    x = to_device(si.gaussian_complex(64, 4096, seed=1), "interleaved")
+    p = fc.Plan(4096, 64, precision="fp16_tc_split")
+    a = p.execute(x)
+    b = p.execute(x)
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.float32), b.view(torch.float32))
+    with pytest.raises(nat.FftcError):
+        fc.Plan(64, 4, precision="fp16_tc")
+
+
+@pytest.mark.parametrize("e", [12, 16])
+def test_precision_workload_full_batch_sampled(e):
+    """n = 2^12 and 2^16 at the workload's batch 2^14, sampled rows vs the oracle."""
+    n, B = 1 << e, 1 << 14
+    x = si.gaussian_complex(B, n, seed=3)
+    rows = np.array([0, 1, B // 2, B - 1])
+    ref = oracle.fft(x[rows].astype(np.complex128))
+    for mode in ("fp16_tc_split", "bf16_tc"):
+        y = _run(x, "interleaved", False, mode)
+        err = rel_l2_rows(y[rows], ref).max()
+        assert err <= bound(mode, n), (mode, n, float(err))
