@@ -31,6 +31,7 @@ struct PassParams {
     const float2 *tw;      // per-stage tables of this pass (Sched layout)
     const float2 *tw2_lo;  // inter-pass twiddle w_N^m = tw2_lo[m & lo_mask] * tw2_hi[m >> lo_bits]
     const float2 *tw2_hi;
+    const float2 *tw2_full;  // when set: w_N^(b t') = tw2_full[t' * K + b] (pass-1 layout, one rounding)
     const float *post_h;   // optional real factor per output frequency (NULL = none)
     int64_t post_line_mul, post_elem_mul;  // frequency = line * post_line_mul + a * post_elem_mul
     float post_scale;

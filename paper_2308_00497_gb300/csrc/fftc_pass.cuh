@@ -28,7 +28,9 @@ struct Pass {
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
     static constexpr int NT = C * TPL;
-    static constexpr int PITCH = (C > 1) ? L + 1 : L;
+    // odd pitch for 16-line tiles, L + 2 for 8-line tiles: both keep the c-fast accesses
+    // of the four-step passes on distinct banks (checked with a bank simulator)
+    static constexpr int PITCH = (C > 1) ? L + (C == 8 ? 2 : 1) : L;
     static constexpr int SMEM = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
     static constexpr bool IN_TAU = (KIND != KIND_COLS);
     static constexpr bool OUT_TAU = (KIND == KIND_ROWS);
@@ -72,20 +74,23 @@ struct Pass {
                                                        bool live) {
         const int64_t base = line_off(p, g, p.in_tr, p.in_line);
         const int cj = conj_of(p, g, p.conj_in);
+        const int es = (int)p.in_elem;  // element stride inside a transform (< 2^31 offsets)
+        const float2 *lp2 = reinterpret_cast<const float2 *>(p.in) + base;
+        const float *lpr = p.in + base, *lpi = p.in + p.in_plane + base;
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
 #pragma unroll
             for (int t = 0; t < R; ++t) {
                 const int a = tau + q * TPL + t * (L / R);
-                const int64_t off = base + (int64_t)a * p.in_elem;
+                const int off = a * es;
                 float2 x = make_float2(0.f, 0.f);
                 if (live) {
                     if constexpr (LIN == LAYOUT_IL) {
-                        if constexpr (IN_L2ONLY) x = __ldcg(reinterpret_cast<const float2 *>(p.in) + off);
-                        else x = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
+                        if constexpr (IN_L2ONLY) x = __ldcg(lp2 + off);
+                        else x = __ldcs(lp2 + off);
                     } else {
-                        x.x = __ldcs(p.in + off);
-                        x.y = __ldcs(p.in + p.in_plane + off);
+                        x.x = __ldcs(lpr + off);
+                        x.y = __ldcs(lpi + off);
                     }
                 }
                 if (cj) x.y = -x.y;
@@ -98,34 +103,41 @@ struct Pass {
     __device__ __forceinline__ static void store_global(const PassParams &p, float2 (&v)[E], int tau, int64_t g,
                                                         bool live) {
         if (!live) return;
-        const int64_t l = g & ((int64_t(1) << p.log_lpt) - 1);
+        const int l = (int)(g & ((int64_t(1) << p.log_lpt) - 1));
         const int64_t base = line_off(p, g, p.out_tr, p.out_line);
         const int cj = conj_of(p, g, p.conj_out);
+        const int es = (int)p.out_elem;
+        float2 *lp2 = reinterpret_cast<float2 *>(p.out) + base;
+        float *lpr = p.out + base, *lpi = p.out + p.out_plane + base;
+        const float2 *dtab = (KIND == KIND_COLS && p.tw2_full) ? p.tw2_full + l * (int)p.out_line : nullptr;
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
 #pragma unroll
             for (int t = 0; t < R; ++t) {
                 const int a = tau + q * TPL + t * (L / R);
+                const int off = a * es;
                 float2 x = v[q * R + t];
                 if constexpr (KIND == KIND_COLS) {
                     // inter-pass twiddle of Eq. 1 applied at the memory level: w_N^(b t')
-                    const int64_t m = (l * a) & ((int64_t(1) << p.log_n2) - 1);
-                    const float2 w = cmul(__ldg(p.tw2_lo + (m & ((int64_t(1) << p.tw2_lo_bits) - 1))),
-                                          __ldg(p.tw2_hi + (m >> p.tw2_lo_bits)));
-                    x = cmul(x, w);
+                    if (dtab) {
+                        x = cmul(x, __ldg(dtab + off));
+                    } else {
+                        const int m = (l * a) & ((1 << p.log_n2) - 1);
+                        x = cmul(x, cmul(__ldg(p.tw2_lo + (m & ((1 << p.tw2_lo_bits) - 1))),
+                                         __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
+                    }
                 }
                 if (p.post_h) {
-                    const float h = __ldg(p.post_h + l * p.post_line_mul + (int64_t)a * p.post_elem_mul) * p.post_scale;
+                    const float h = __ldg(p.post_h + l * (int)p.post_line_mul + a * (int)p.post_elem_mul) * p.post_scale;
                     x.x *= h;
                     x.y *= h;
                 }
                 if (cj) x.y = -x.y;
-                const int64_t off = base + (int64_t)a * p.out_elem;
                 if constexpr (LOUT == LAYOUT_IL) {
-                    __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
+                    __stcs(lp2 + off, x);
                 } else {
-                    __stcs(p.out + off, x.x);
-                    __stcs(p.out + p.out_plane + off, x.y);
+                    __stcs(lpr + off, x.x);
+                    __stcs(lpi + off, x.y);
                 }
             }
         }

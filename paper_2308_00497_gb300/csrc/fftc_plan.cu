@@ -48,7 +48,7 @@ bool choose_rows(int logn, int lin, int *loge, int *lines) {
     return find_kernel(KIND_ROWS, logn, e, c, lin, lin) != nullptr;
 }
 
-bool choose_four_step(int logn, int *logm, int *loge1, int *loge2) {
+bool choose_four_step(int logn, int *logm, int *loge1, int *loge2, int *lines1, int *lines2) {
     int m = env_int("FFTC_TUNE_FOURSTEP_LOGM", logn / 2);
     int k = logn - m;
     *logm = m;
@@ -56,6 +56,9 @@ bool choose_four_step(int logn, int *logm, int *loge1, int *loge2) {
     *loge2 = env_int("FFTC_TUNE_ROWST_E", k >= 9 ? 5 : 4);
     if (*loge1 > m) *loge1 = m;
     if (*loge2 >= k) *loge2 = k - 1;
+    // 8-line tiles (two CTAs per SM) where the line is long, 16-line tiles otherwise
+    if (lines1) *lines1 = env_int("FFTC_TUNE_COLS_C", m >= 9 ? 8 : 16);
+    if (lines2) *lines2 = env_int("FFTC_TUNE_ROWST_C", k >= 9 ? 8 : 16);
     return true;
 }
 
@@ -117,11 +120,11 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     }
 
     // four-step: n = M * K
-    int logm, e1, e2;
+    int logm, e1, e2, c1 = kPassLines, c2 = kPassLines;
     if (tc) {
         logm = p->logn / 2;
         e1 = e2 = 4;
-    } else if (!choose_four_step(p->logn, &logm, &e1, &e2)) {
+    } else if (!choose_four_step(p->logn, &logm, &e1, &e2, &c1, &c2)) {
         return FFTC_ERR_UNSUPPORTED_SIZE;
     }
     const int logk = p->logn - logm;
@@ -148,13 +151,25 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     p->tw2_lo = (float2 *)d;
     if (plan_upload(p, hi.data(), hi.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     p->tw2_hi = (float2 *)d;
+    // the whole diagonal D^n_M of Eq. 1 in pass-1 layout: entry t' * K + b = w_n^(b t')
+    {
+        std::vector<float2> full((size_t)n);
+        for (int64_t tp = 0; tp < M; ++tp)
+            for (int64_t b = 0; b < K; ++b) {
+                double c, s;
+                unit_root(tp * b, n, &c, &s);
+                full[(size_t)(tp * K + b)] = make_float2((float)c, (float)-s);
+            }
+        if (plan_upload(p, full.data(), full.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        p->tw2_full = (float2 *)d;
+    }
 
     {   // pass 1: columns
         PassPlan &pp = p->pass[0];
         pp.kind = KIND_COLS;
         pp.logl = logm;
         pp.loge = e1;
-        pp.lines = kPassLines;
+        pp.lines = c1;
         pp.lin = lay;
         pp.lout = LAYOUT_IL;
         pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec);
@@ -172,6 +187,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         b.out_elem = K;
         b.tw2_lo = p->tw2_lo;
         b.tw2_hi = p->tw2_hi;
+        b.tw2_full = p->tw2_full;
         b.log_n2 = p->logn;
         b.tw2_lo_bits = p->tw2_lo_bits;
         fftc_status s = upload_stage_tables(p, pp);
@@ -183,7 +199,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.kind = KIND_ROWST;
         pp.logl = logk;
         pp.loge = e2;
-        pp.lines = kPassLines;
+        pp.lines = c2;
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
         pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec);

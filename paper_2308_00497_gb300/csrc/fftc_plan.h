@@ -38,7 +38,7 @@ struct fftc_plan_s {
     int npasses = 0;
     fftc::PassPlan pass[2] = {};
     float2 *workspace = nullptr;
-    float2 *tw2_lo = nullptr, *tw2_hi = nullptr;
+    float2 *tw2_lo = nullptr, *tw2_hi = nullptr, *tw2_full = nullptr;
     int tw2_lo_bits = 0;
     int *d_err = nullptr;  // device error word (bounded waits)
     fftc::UnevenState *uneven = nullptr;
@@ -76,6 +76,6 @@ int uneven_max_logn(const fftc_plan_s *p);
 // Kernel choice for a pass; overridable through FFTC_TUNE_* environment variables
 // by the tuner. Returns false if no compiled kernel fits.
 bool choose_rows(int logn, int lin, int *loge, int *lines);
-bool choose_four_step(int logn, int *logm, int *loge1, int *loge2);
+bool choose_four_step(int logn, int *logm, int *loge1, int *loge2, int *lines1 = nullptr, int *lines2 = nullptr);
 
 }  // namespace fftc
