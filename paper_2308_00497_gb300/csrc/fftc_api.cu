@@ -21,14 +21,14 @@ namespace fftc {
 // ---------------------------------------------------------------------------
 // schedule mirror and registry
 // ---------------------------------------------------------------------------
-HostSched host_sched(int logl, int loge) {
+HostSched host_sched(int logl, int loge, bool rem_first) {
     HostSched h{};
     if (loge > logl) loge = logl;
     h.S = (logl + loge - 1) / loge;
     const int rem = logl % loge;
     int acc = 0;
     for (int s = 0; s < h.S; ++s) {
-        h.lr[s] = (s == 0 && rem) ? rem : loge;
+        h.lr[s] = (rem && (rem_first ? s == 0 : s == h.S - 1)) ? rem : loge;
         h.lns[s] = acc;
         acc += h.lr[s];
     }
@@ -38,11 +38,11 @@ HostSched host_sched(int logl, int loge) {
     return h;
 }
 
-const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec) {
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec, int logx) {
     for (int i = 0; i < kernel_count(); ++i) {
         const KernelEntry *e = kernel_at(i);
         if (e->kind == kind && e->logl == logl && e->loge == loge && e->lines == lines && e->lin == lin &&
-            e->lout == lout && e->prec == prec)
+            e->lout == lout && e->prec == prec && e->logx == logx)
             return e;
     }
     return nullptr;
@@ -90,8 +90,8 @@ static float2 omega_f32(int64_t e, int64_t L) {
     return make_float2((float)c, (float)-s);
 }
 
-void stage_twiddles(int logl, int loge, std::vector<float2> &out) {
-    HostSched h = host_sched(logl, loge);
+void stage_twiddles(int logl, int loge, std::vector<float2> &out, bool rem_first) {
+    HostSched h = host_sched(logl, loge, rem_first);
     out.assign(h.tw_total > 0 ? h.tw_total : 1, make_float2(1.f, 0.f));
     int off = 0;
     for (int s = 1; s < h.S; ++s) {
@@ -242,7 +242,7 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
     }
     for (int i = 0; i < plan->npasses && !plan->uneven; ++i) {
         const PassPlan &pp = plan->pass[i];
-        HostSched h = host_sched(pp.logl, pp.loge);
+        HostSched h = host_sched(pp.logl, pp.loge, plan->precision != FFTC_FP32);
         for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];
     }
     if (radices)

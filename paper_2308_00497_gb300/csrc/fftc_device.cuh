@@ -106,13 +106,14 @@ __host__ __device__ __forceinline__ void dft(float2 *a) {
 
 // ---------------------------------------------------------------------------
 // Radix schedule of one line of length L = 2^LOGL with E = 2^LOGE elements per
-// thread: S stages, the first taking the remainder radix 2^(LOGL mod LOGE) when
-// LOGE does not divide LOGL, all others radix E. Stage s has sub-transform length
-// Ns = product of the earlier radices (the Stockham "Ns").
-// Per-stage twiddle tables (stage s >= 1) hold w_{Ns R}^{t k} at [(t-1) Ns + k],
-// t = 1..R-1, k < Ns, concatenated in stage order.
+// thread: S stages of radix E, except that when LOGE does not divide LOGL one stage
+// takes the remainder radix 2^(LOGL mod LOGE): the last stage (REM_FIRST = false,
+// the CUDA-core kernels) or the first (REM_FIRST = true, the tensor-core kernels).
+// Stage s has sub-transform length Ns = product of the earlier radices (the
+// Stockham "Ns"). Per-stage twiddle tables (stage s >= 1) hold w_{Ns R}^{t k} at
+// [(t-1) Ns + k], t = 1..R-1, k < Ns, concatenated in stage order.
 // ---------------------------------------------------------------------------
-template <int LOGL, int LOGE>
+template <int LOGL, int LOGE, bool REM_FIRST = false>
 struct Sched {
     static_assert(LOGE >= 1 && LOGE <= LOGL, "need 2 <= E <= L");
     static constexpr int L = 1 << LOGL;
@@ -120,8 +121,14 @@ struct Sched {
     static constexpr int TPL = L / E;  // threads per line
     static constexpr int S = (LOGL + LOGE - 1) / LOGE;
     static constexpr int REM = LOGL % LOGE;
-    __host__ __device__ static constexpr int lr(int s) { return (s == 0 && REM) ? REM : LOGE; }
-    __host__ __device__ static constexpr int lns(int s) { return s == 0 ? 0 : lr(0) + (s - 1) * LOGE; }
+    __host__ __device__ static constexpr int lr(int s) {
+        return (REM && (REM_FIRST ? s == 0 : s == S - 1)) ? REM : LOGE;
+    }
+    __host__ __device__ static constexpr int lns(int s) {
+        int acc = 0;
+        for (int i = 0; i < s; ++i) acc += lr(i);
+        return acc;
+    }
     __host__ __device__ static constexpr int tw_off(int s) {
         int o = 0;
         for (int i = 1; i < s; ++i) o += ((1 << lr(i)) - 1) << lns(i);
@@ -129,19 +136,5 @@ struct Sched {
     }
     static constexpr int tw_total = tw_off(S);
 };
-
-// Swizzle of the shared-memory exchange written by a stage with log2 Ns = lo and
-// log2 (Ns R) = hi. It permutes words inside aligned groups of 16 (so no padding)
-// and XORs into the bank bits [lo, min(4, hi)) the address bits that the write
-// pattern (j/Ns) Ns R + j mod Ns + t Ns would otherwise leave on one bank; the
-// next stage reads 16 consecutive words per half-warp, which any such
-// permutation keeps on distinct banks.
-__host__ __device__ __forceinline__ int swz(int a, int lo, int hi) {
-    const int top = hi < 4 ? hi : 4;
-    const int nfree = top - lo;
-    if (nfree <= 0) return a;
-    const int src = hi > 4 ? hi : 4;
-    return a ^ (((a >> src) & ((1 << nfree) - 1)) << lo);
-}
 
 }  // namespace fftc

@@ -58,10 +58,12 @@ struct KernelEntry {
     LaunchFn launch;
     PrepareFn prepare;
     int prec;  // fftc_precision of the radix stages (0 = FP32 on CUDA cores)
+    int logx;  // four-step passes: log2 of the compile-time element stride (0 = runtime)
 };
 
 // Registry of compiled pass kernels (one table per instantiation unit).
-const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec = 0);
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec = 0,
+                               int logx = 0);
 int kernel_count();
 const KernelEntry *kernel_at(int i);
 
@@ -72,6 +74,6 @@ struct HostSched {
     int lns[32];
     int tw_total;
 };
-HostSched host_sched(int logl, int loge);
+HostSched host_sched(int logl, int loge, bool rem_first = false);
 
 }  // namespace fftc

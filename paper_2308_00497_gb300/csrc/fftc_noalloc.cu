@@ -52,11 +52,12 @@ fftc_status setup_device(int dev, DeviceSetup &d) {
     std::vector<float2> host((size_t)kNumLogs * kTabPerLog, make_float2(0.f, 0.f));
     for (int logn = kMinLog; logn <= kMaxLog; ++logn) {
         SizeSetup &s = d.size[logn - kMinLog];
-        if (!choose_four_step(logn, &s.logm, &s.e1, &s.e2)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        int c1 = 16, c2 = 16;
+        if (!choose_four_step(logn, &s.logm, &s.e1, &s.e2, &c1, &c2)) return FFTC_ERR_UNSUPPORTED_SIZE;
         const int logk = logn - s.logm;
         for (int lay = 0; lay < 2; ++lay) {
-            s.k1[lay] = find_kernel(KIND_COLS, s.logm, s.e1, 16, lay, LAYOUT_IL);
-            s.k2[lay] = find_kernel(KIND_ROWST, logk, s.e2, 16, LAYOUT_IL, lay);
+            s.k1[lay] = find_kernel(KIND_COLS, s.logm, s.e1, c1, lay, LAYOUT_IL, 0, logk);
+            s.k2[lay] = find_kernel(KIND_ROWST, logk, s.e2, c2, LAYOUT_IL, lay, 0, s.logm);
             if (!s.k1[lay] || !s.k2[lay]) return FFTC_ERR_UNSUPPORTED_SIZE;
             if (s.k1[lay]->prepare() != cudaSuccess || s.k2[lay]->prepare() != cudaSuccess) return FFTC_ERR_CUDA;
         }

@@ -11,11 +11,21 @@
 // The first stage reads HBM directly and the last one writes HBM directly, both
 // coalesced, so one pass moves each element through HBM once.
 //
+// Shared-memory layout. Stage 0 has radix E and Ns = 1, so its writes land on
+// j E + t, E words apart across threads: the first exchange therefore stores word a
+// at a + (a >> LOGE) (one skew word per E words). Every later stage has Ns >= E >= 16
+// and writes runs of consecutive words, so later exchanges use the identity layout.
+// With both layouts every shared access of a thread is a per-thread base plus a
+// compile-time offset, and a half-warp touches 16 distinct banks (checked with a bank
+// simulator for E = 16, L >= 256 and E = 32, L >= 512).
+//
 // Thread <-> (line c, position tau) mapping, chosen per stage:
 //   tau-fast: consecutive threads walk one line (coalesced for contiguous lines);
 //   c-fast:   consecutive threads walk C lines at the same position (coalesced for
-//             column access at unit line stride; conflict-free in shared memory
-//             because the line pitch L + 1 is odd).
+//             column access at unit line stride; the line pitch keeps it conflict-free).
+//
+// Element strides: 1 for contiguous lines; for the four-step passes the stride is
+// the other factor 2^LOGX of n = M K, a compile-time constant when LOGX > 0.
 #pragma once
 
 #include "fftc_device.cuh"
@@ -23,14 +33,17 @@
 
 namespace fftc {
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false>
+__host__ __device__ constexpr int pass_pitch(int line_words, int lines) {
+    return lines == 1 ? line_words : line_words + (lines == 8 ? 2 : 1);
+}
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0>
 struct Pass {
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
     static constexpr int NT = C * TPL;
-    // odd pitch for 16-line tiles, L + 2 for 8-line tiles: both keep the c-fast accesses
-    // of the four-step passes on distinct banks (checked with a bank simulator)
-    static constexpr int PITCH = (C > 1) ? L + (C == 8 ? 2 : 1) : L;
+    static constexpr int LINE_WORDS = L + (L >> LOGE);
+    static constexpr int PITCH = pass_pitch(LINE_WORDS, C);
     static constexpr int SMEM = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
     static constexpr bool IN_TAU = (KIND != KIND_COLS);
     static constexpr bool OUT_TAU = (KIND == KIND_ROWS);
@@ -49,6 +62,12 @@ struct Pass {
     static constexpr bool WARP_SYNC = all_tau() && TPL <= 32 && (32 % TPL) == 0;
     static constexpr int REG_TARGET = E >= 32 ? 128 : (E >= 16 ? 80 : 64);
     static constexpr int MINB = (65536 / (NT * REG_TARGET)) > 0 ? (65536 / (NT * REG_TARGET)) : 1;
+    // element strides: compile-time unless LOGX == 0 for a four-step kind
+    static constexpr int ES_IN_CT = (KIND == KIND_COLS) ? (LOGX ? (1 << LOGX) : 0) : 1;
+    static constexpr int ES_OUT_CT = (KIND == KIND_ROWS) ? 1 : (LOGX ? (1 << LOGX) : 0);
+    // the four-step workspace is written in the same launch in persistent mode: read it
+    // from L2 only, never through a possibly stale L1 line
+    static constexpr bool IN_L2ONLY = (KIND == KIND_ROWST);
 
     __device__ __forceinline__ static void sync() {
         if constexpr (WARP_SYNC)
@@ -65,32 +84,29 @@ struct Pass {
         if constexpr (IDX) return __ldg(p.line_conj + g);
         return flag;
     }
-    // the four-step workspace is written in the same launch in persistent mode: read it
-    // from L2 only, never through a possibly stale L1 line
-    static constexpr bool IN_L2ONLY = (KIND == KIND_ROWST);
 
     template <int R>
     __device__ __forceinline__ static void load_global(const PassParams &p, float2 (&v)[E], int tau, int64_t g,
                                                        bool live) {
         const int64_t base = line_off(p, g, p.in_tr, p.in_line);
         const int cj = conj_of(p, g, p.conj_in);
-        const int es = (int)p.in_elem;  // element stride inside a transform (< 2^31 offsets)
-        const float2 *lp2 = reinterpret_cast<const float2 *>(p.in) + base;
-        const float *lpr = p.in + base, *lpi = p.in + p.in_plane + base;
+        const int es = ES_IN_CT ? ES_IN_CT : (int)p.in_elem;
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
+            const int64_t b = base + (int64_t)(tau + q * TPL) * es;
+            const float2 *p2 = reinterpret_cast<const float2 *>(p.in) + b;
+            const float *pr = p.in + b, *pi = p.in + p.in_plane + b;
 #pragma unroll
             for (int t = 0; t < R; ++t) {
-                const int a = tau + q * TPL + t * (L / R);
-                const int off = a * es;
+                const int off = t * (L / R) * es;  // compile-time when the stride is
                 float2 x = make_float2(0.f, 0.f);
                 if (live) {
                     if constexpr (LIN == LAYOUT_IL) {
-                        if constexpr (IN_L2ONLY) x = __ldcg(lp2 + off);
-                        else x = __ldcs(lp2 + off);
+                        if constexpr (IN_L2ONLY) x = __ldcg(p2 + off);
+                        else x = __ldcs(p2 + off);
                     } else {
-                        x.x = __ldcs(lpr + off);
-                        x.y = __ldcs(lpi + off);
+                        x.x = __ldcs(pr + off);
+                        x.y = __ldcs(pi + off);
                     }
                 }
                 if (cj) x.y = -x.y;
@@ -106,38 +122,42 @@ struct Pass {
         const int l = (int)(g & ((int64_t(1) << p.log_lpt) - 1));
         const int64_t base = line_off(p, g, p.out_tr, p.out_line);
         const int cj = conj_of(p, g, p.conj_out);
-        const int es = (int)p.out_elem;
-        float2 *lp2 = reinterpret_cast<float2 *>(p.out) + base;
-        float *lpr = p.out + base, *lpi = p.out + p.out_plane + base;
-        const float2 *dtab = (KIND == KIND_COLS && p.tw2_full) ? p.tw2_full + l * (int)p.out_line : nullptr;
+        const int es = ES_OUT_CT ? ES_OUT_CT : (int)p.out_elem;
+        const float2 *dtab = nullptr;
+        if constexpr (KIND == KIND_COLS) dtab = p.tw2_full ? p.tw2_full + l * (int)p.out_line : nullptr;
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
+            const int a0 = tau + q * TPL;
+            const int64_t b = base + (int64_t)a0 * es;
+            float2 *p2 = reinterpret_cast<float2 *>(p.out) + b;
+            float *pr = p.out + b, *pi = p.out + p.out_plane + b;
 #pragma unroll
             for (int t = 0; t < R; ++t) {
-                const int a = tau + q * TPL + t * (L / R);
-                const int off = a * es;
+                const int off = t * (L / R) * es;
                 float2 x = v[q * R + t];
                 if constexpr (KIND == KIND_COLS) {
                     // inter-pass twiddle of Eq. 1 applied at the memory level: w_N^(b t')
                     if (dtab) {
-                        x = cmul(x, __ldg(dtab + off));
+                        x = cmul(x, __ldg(dtab + a0 * es + off));
                     } else {
+                        const int a = a0 + t * (L / R);
                         const int m = (l * a) & ((1 << p.log_n2) - 1);
                         x = cmul(x, cmul(__ldg(p.tw2_lo + (m & ((1 << p.tw2_lo_bits) - 1))),
                                          __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
                     }
                 }
                 if (p.post_h) {
+                    const int a = a0 + t * (L / R);
                     const float h = __ldg(p.post_h + l * (int)p.post_line_mul + a * (int)p.post_elem_mul) * p.post_scale;
                     x.x *= h;
                     x.y *= h;
                 }
                 if (cj) x.y = -x.y;
                 if constexpr (LOUT == LAYOUT_IL) {
-                    __stcs(lp2 + off, x);
+                    __stcs(p2 + off, x);
                 } else {
-                    __stcs(lpr + off, x.x);
-                    __stcs(lpi + off, x.y);
+                    __stcs(pr + off, x.x);
+                    __stcs(pi + off, x.y);
                 }
             }
         }
@@ -156,18 +176,25 @@ struct Pass {
         if constexpr (s == 0) {
             load_global<R>(p, v, tau, g, live);
         } else {
-            constexpr int PLO = Sc::lns(s - 1);
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
+                const int j = tau + q * TPL;
+                if constexpr (s == 1) {  // skewed layout of the first exchange (L/R is a multiple of E)
+                    const float2 *src = line + j + (j >> LOGE);
 #pragma unroll
-                for (int t = 0; t < R; ++t) v[q * R + t] = line[swz(tau + q * TPL + t * (L / R), PLO, LNS)];
+                    for (int t = 0; t < R; ++t) v[q * R + t] = src[t * (L / R) + ((t * (L / R)) >> LOGE)];
+                } else {
+                    const float2 *src = line + j;
+#pragma unroll
+                    for (int t = 0; t < R; ++t) v[q * R + t] = src[t * (L / R)];
+                }
             }
             const float2 *tw = p.tw + Sc::tw_off(s);
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
-                const int k = (tau + q * TPL) & (NS - 1);
+                const float2 *twk = tw + ((tau + q * TPL) & (NS - 1));
 #pragma unroll
-                for (int t = 1; t < R; ++t) v[q * R + t] = cmul(v[q * R + t], __ldg(tw + (t - 1) * NS + k));
+                for (int t = 1; t < R; ++t) v[q * R + t] = cmul(v[q * R + t], __ldg(twk + (t - 1) * NS));
             }
         }
 #pragma unroll
@@ -178,9 +205,15 @@ struct Pass {
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
                 const int j = tau + q * TPL;
-                const int b = ((j >> LNS) << (LNS + LR)) + (j & (NS - 1));
+                if constexpr (s == 0) {  // Ns = 1, R = E: word j E + t, skewed to j (E + 1) + t
+                    float2 *dst = line + j * (E + 1);
 #pragma unroll
-                for (int t = 0; t < R; ++t) line[swz(b + t * NS, LNS, LNS + LR)] = v[q * R + t];
+                    for (int t = 0; t < R; ++t) dst[t] = v[q * R + t];
+                } else {
+                    float2 *dst = line + ((j >> LNS) << (LNS + LR)) + (j & (NS - 1));
+#pragma unroll
+                    for (int t = 0; t < R; ++t) dst[t * NS] = v[q * R + t];
+                }
             }
             sync();
             stage<s + 1>(p, sm, v, tid, g0);
@@ -202,35 +235,46 @@ struct Pass {
     }
 };
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
-__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT>::NT, Pass<LOGL, LOGE, C, KIND, LIN, LOUT>::MINB)
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
+__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::NT,
+                                  Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::MINB)
     k_pass(const __grid_constant__ PassParams p) {
-    Pass<LOGL, LOGE, C, KIND, LIN, LOUT>::run(p);
+    Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::run(p);
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
 cudaError_t launch_pass(const PassParams &p, cudaStream_t st) {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
     const int64_t blocks = (p.total_lines + C - 1) / C;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
+    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
 cudaError_t prepare_pass() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
     if (P::SMEM <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                P::SMEM);
+    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX = 0>
 constexpr KernelEntry entry() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT>;
-    return KernelEntry{KIND, LOGL, LOGE, C, LIN, LOUT, P::NT, P::SMEM,
-                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT>, 0};
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
+    return KernelEntry{KIND,
+                       LOGL,
+                       LOGE,
+                       C,
+                       LIN,
+                       LOUT,
+                       P::NT,
+                       P::SMEM,
+                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
+                       &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
+                       0,
+                       LOGX};
 }
 
 }  // namespace fftc

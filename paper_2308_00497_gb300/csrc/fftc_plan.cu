@@ -64,7 +64,7 @@ bool choose_four_step(int logn, int *logm, int *loge1, int *loge2, int *lines1, 
 
 static fftc_status upload_stage_tables(fftc_plan_s *p, PassPlan &pp) {
     std::vector<float2> tw;
-    stage_twiddles(pp.logl, pp.loge, tw);
+    stage_twiddles(pp.logl, pp.loge, tw, p->precision != FFTC_FP32);  // tensor-core kernels: remainder first
     void *d = nullptr;
     if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     pp.tw = (float2 *)d;
@@ -172,7 +172,8 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lines = c1;
         pp.lin = lay;
         pp.lout = LAYOUT_IL;
-        pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec);
+        pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
+        if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.in_plane = plane;
@@ -202,7 +203,8 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lines = c2;
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
-        pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec);
+        pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
+        if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.in_plane = 0;

@@ -65,7 +65,7 @@ cudaError_t plan_alloc(fftc_plan_s *p, size_t bytes, void **out);
 cudaError_t plan_upload(fftc_plan_s *p, const void *host, size_t bytes, void **out);
 
 void unit_root(int64_t m, int64_t L, double *cosv, double *sinv);
-void stage_twiddles(int logl, int loge, std::vector<float2> &out);
+void stage_twiddles(int logl, int loge, std::vector<float2> &out, bool rem_first = false);
 
 // uneven batches (fftc_uneven.cu)
 fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir, const int64_t *off);

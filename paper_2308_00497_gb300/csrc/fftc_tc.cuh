@@ -84,7 +84,7 @@ __device__ __forceinline__ float sin16(int m) { return cos16(m - 4); }
 
 template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
 struct TcPass {
-    using Sc = Sched<LOGL, 4>;
+    using Sc = Sched<LOGL, 4, true>;  // leftover radix first, then radix-16 stages
     using Ops = TcOps<PREC>;
     static constexpr int L = 1 << LOGL, S = Sc::S, NT = 256, NW = NT / 32;
     static constexpr int ROW = L / 16;            // one row per input index t of a radix-16 stage
@@ -281,8 +281,8 @@ cudaError_t prepare_tc() {
 template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
 constexpr KernelEntry tc_entry() {
     using P = TcPass<LOGL, C, KIND, LIN, LOUT, PREC>;
-    return KernelEntry{KIND,        LOGL, 4, C, LIN, LOUT, P::NT, P::SMEM, &launch_tc<LOGL, C, KIND, LIN, LOUT, PREC>,
-                       &prepare_tc<LOGL, C, KIND, LIN, LOUT, PREC>, PREC};
+    return KernelEntry{KIND,   LOGL,   4, C, LIN, LOUT, P::NT, P::SMEM, &launch_tc<LOGL, C, KIND, LIN, LOUT, PREC>,
+                       &prepare_tc<LOGL, C, KIND, LIN, LOUT, PREC>, PREC, 0};
 }
 
 }  // namespace fftc
