@@ -226,7 +226,10 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
         passes, _ = p.info()
         launches += passes * cnt
         n = 1 << e
-        names = ["rows"] if passes == 1 else ["cols", "rowst"]
+        if passes == 2:
+            names = ["cols", "rowst"]
+        else:  # one launch: a single-pass kernel, or both four-step passes in one L2-resident launch
+            names = ["rows"] if n <= (1 << 13) else ["fourstep_l2"]
         for i, nm in enumerate(names):
             k = kinds.setdefault(nm, {"ms": 0.0, "launches": 0})
             k["ms"] += pm[i]

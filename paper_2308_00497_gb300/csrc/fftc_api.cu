@@ -240,7 +240,8 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
     } else if (passes) {
         *passes = plan->npasses;
     }
-    for (int i = 0; i < plan->npasses && !plan->uneven; ++i) {
+    const int nsched = plan->fs ? 2 : plan->npasses;
+    for (int i = 0; i < nsched && !plan->uneven; ++i) {
         const PassPlan &pp = plan->pass[i];
         HostSched h = host_sched(pp.logl, pp.loge, plan->precision != FFTC_FP32);
         for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];

@@ -153,7 +153,9 @@ struct Pass {
                     x.y *= h;
                 }
                 if (cj) x.y = -x.y;
-                if constexpr (LOUT == LAYOUT_IL) {
+                if constexpr (KIND == KIND_COLS) {
+                    __stcg(p2 + off, x);  // workspace: keep it in L2 for pass 2
+                } else if constexpr (LOUT == LAYOUT_IL) {
                     __stcs(p2 + off, x);
                 } else {
                     __stcs(pr + off, x.x);

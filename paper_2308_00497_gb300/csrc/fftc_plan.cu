@@ -130,8 +130,11 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     const int logk = p->logn - logm;
     const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
     p->npasses = 2;
-    if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
-    p->workspace = (float2 *)d;
+    const bool l2res = !tc && fs_available(p->logn, lay);
+    if (!l2res) {  // the L2-resident executor owns a small workspace ring instead
+        if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        p->workspace = (float2 *)d;
+    }
 
     // inter-pass twiddle w_n^m as a product of two small tables
     p->tw2_lo_bits = (p->logn + 1) / 2;
@@ -223,6 +226,11 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         if (s != FFTC_OK) return s;
         if ((s = prepare(pp)) != FFTC_OK) return s;
     }
+    if (l2res) {
+        fftc_status s = fs_build(p);
+        if (s != FFTC_OK) return s;
+        p->npasses = 1;  // one HBM round trip: the intermediate stays in L2
+    }
     return FFTC_OK;
 }
 
@@ -242,6 +250,11 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     if (p->precision != FFTC_FP32 && post_h) return FFTC_ERR_INVALID_VALUE;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
     if (ev) cudaEventRecord(ev[0], st);
+    if (p->fs) {
+        fftc_status s = fs_run(p, in, out, post_h, post_scale, st);
+        if (ev) cudaEventRecord(ev[1], st);
+        return s;
+    }
     if (p->npasses == 1) {
         PassParams a = p->pass[0].base;
         a.in = (const float *)in;
@@ -272,7 +285,10 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     return FFTC_OK;
 }
 
-void plan_destroy_extra(fftc_plan_s *p) { uneven_free(p); }
+void plan_destroy_extra(fftc_plan_s *p) {
+    uneven_free(p);
+    fs_free(p);
+}
 
 void plan_probe_free(fftc_plan_s *p) {
     for (cudaEvent_t e : p->probe_events) cudaEventDestroy(e);

@@ -21,6 +21,7 @@ struct PassPlan {
 };
 
 struct UnevenState;  // persistent uneven-batch executor (fftc_uneven.cu)
+struct FsState;      // L2-resident four-step executor (fftc_fourstep_l2.cu)
 struct TcState;      // tensor-core radix-16 executor (fftc_tc.cu)
 
 }  // namespace fftc
@@ -43,6 +44,7 @@ struct fftc_plan_s {
     int *d_err = nullptr;  // device error word (bounded waits)
     fftc::UnevenState *uneven = nullptr;
     fftc::TcState *tc = nullptr;
+    fftc::FsState *fs = nullptr;
     std::vector<void *> dev_allocs;
     // timing probe: events[slot * 3 + i] before pass i (i < npasses) and after the last
     std::vector<cudaEvent_t> probe_events;
@@ -72,6 +74,12 @@ fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const 
 fftc_status uneven_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
 void uneven_free(fftc_plan_s *p);
 int uneven_max_logn(const fftc_plan_s *p);
+
+// L2-resident four-step (fftc_fourstep_l2.cu)
+bool fs_available(int logn, int lay);
+fftc_status fs_build(fftc_plan_s *p);
+fftc_status fs_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale, cudaStream_t st);
+void fs_free(fftc_plan_s *p);
 
 // Kernel choice for a pass; overridable through FFTC_TUNE_* environment variables
 // by the tuner. Returns false if no compiled kernel fits.

@@ -151,3 +151,36 @@ def test_misaligned_and_null_pointers():
     assert lib.fftc_destroy(h) == nat.OK
     assert lib.fftc_destroy(h) == nat.ERR_INVALID_PLAN   # a destroyed plan is recognised
     assert lib.fftc_execute(h, ctypes.c_void_p(base), ctypes.c_void_p(base), None) == nat.ERR_INVALID_PLAN
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_l2_resident_many_groups_ring_wrap_and_tail(monkeypatch, layout, inverse):
+    """Small groups (1 MiB), a two-slot ring and a partial last group: every row checked."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_L2_GROUP_MB", "1")
+    monkeypatch.setenv("FFTC_L2_RING", "2")
+    n, B = 1 << 16, 9          # groups of 2 transforms: 5 groups, the last one partial
+    x = si.uniform_complex(B, n, seed=77)
+    p = fc.Plan(n, B, layout, inverse)
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    ref = oracle.fft(x.astype(np.complex128), inverse=inverse)
+    assert rel_l2_rows(y, ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [14, 15, 17, 20])
+def test_l2_resident_matches_two_launch_path(monkeypatch, e):
+    import paper_2308_00497_gb300 as fc
+    n = 1 << e
+    B = max(2, (1 << 22) // n)
+    x = to_device(si.uniform_complex(B, n, seed=e), "interleaved")
+    a = fc.Plan(n, B).execute(x)
+    monkeypatch.setenv("FFTC_L2_RESIDENT", "0")
+    q = fc.Plan(n, B)
+    assert q.info()[0] == 2
+    b = q.execute(x)
+    torch.cuda.synchronize()
+    err = rel_l2_rows(a.cpu().numpy(), b.cpu().numpy().astype(np.complex128))
+    assert err.max() <= 2 * tol_fp32(n)
