@@ -178,7 +178,8 @@ static int env_int_fs(const char *name, int dflt) {
     return (v && *v) ? atoi(v) : dflt;
 }
 
-bool fs_available(int logn, int lay) { return env_int_fs("FFTC_L2_RESIDENT", 1) != 0 && find_fs(logn, lay) != nullptr; }
+// Off by default until it beats the two-launch path (FFTC_L2_RESIDENT=1 enables it).
+bool fs_available(int logn, int lay) { return env_int_fs("FFTC_L2_RESIDENT", 0) != 0 && find_fs(logn, lay) != nullptr; }
 
 void fs_free(fftc_plan_s *p) {
     delete p->fs;

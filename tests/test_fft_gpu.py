@@ -126,8 +126,8 @@ def test_plan_info_and_bytes():
     assert passes == 1 and int(np.prod(radices)) == 1024
     assert p.bytes() == 1024 * 4 * 8
     q = fc.Plan(1 << 20, 1, "split", True)
-    passes, radices = q.info()   # four-step with the intermediate kept in L2: one HBM pass
-    assert passes == 1 and int(np.prod(radices)) == 1 << 20
+    passes, radices = q.info()   # four-step: two HBM passes
+    assert passes == 2 and int(np.prod(radices)) == 1 << 20
 
 
 def test_empty_batch_is_a_noop():
@@ -158,6 +158,7 @@ def test_misaligned_and_null_pointers():
 def test_l2_resident_many_groups_ring_wrap_and_tail(monkeypatch, layout, inverse):
     """Small groups (1 MiB), a two-slot ring and a partial last group: every row checked."""
     import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_L2_RESIDENT", "1")
     monkeypatch.setenv("FFTC_L2_GROUP_MB", "1")
     monkeypatch.setenv("FFTC_L2_RING", "2")
     n, B = 1 << 16, 9          # groups of 2 transforms: 5 groups, the last one partial
@@ -176,7 +177,10 @@ def test_l2_resident_matches_two_launch_path(monkeypatch, e):
     n = 1 << e
     B = max(2, (1 << 22) // n)
     x = to_device(si.uniform_complex(B, n, seed=e), "interleaved")
-    a = fc.Plan(n, B).execute(x)
+    monkeypatch.setenv("FFTC_L2_RESIDENT", "1")
+    pa = fc.Plan(n, B)
+    assert pa.info()[0] == 1
+    a = pa.execute(x)
     monkeypatch.setenv("FFTC_L2_RESIDENT", "0")
     q = fc.Plan(n, B)
     assert q.info()[0] == 2
