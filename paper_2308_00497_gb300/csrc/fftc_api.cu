@@ -38,12 +38,21 @@ HostSched host_sched(int logl, int loge, bool rem_first) {
     return h;
 }
 
-const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec, int logx) {
+const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec, int logx,
+                               int pipe) {
     for (int i = 0; i < kernel_count(); ++i) {
         const KernelEntry *e = kernel_at(i);
         if (e->kind == kind && e->logl == logl && e->loge == loge && e->lines == lines && e->lin == lin &&
-            e->lout == lout && e->prec == prec && e->logx == logx)
+            e->lout == lout && e->prec == prec && e->logx == logx && e->pipe == pipe)
             return e;
+    }
+    return nullptr;
+}
+
+const KernelEntry *find_pipe_rows(int logl, int lay) {
+    for (int i = 0; i < kernel_count(); ++i) {
+        const KernelEntry *e = kernel_at(i);
+        if (e->pipe > 0 && e->kind == KIND_ROWS && e->logl == logl && e->lin == lay) return e;
     }
     return nullptr;
 }

@@ -46,6 +46,7 @@ struct PassParams {
     // persistent launches: when set, `in` / `out` hold byte offsets into the launch's
     // user input / output buffers instead of pointers
     int32_t in_user, out_user;
+    int *err;  // device error word of the plan (bounded waits that gave up)
 };
 
 typedef cudaError_t (*LaunchFn)(const PassParams &, cudaStream_t);
@@ -59,11 +60,14 @@ struct KernelEntry {
     PrepareFn prepare;
     int prec;  // fftc_precision of the radix stages (0 = FP32 on CUDA cores)
     int logx;  // four-step passes: log2 of the compile-time element stride (0 = runtime)
+    int pipe;  // > 0: persistent kernel fed by bulk copies through `pipe` landing buffers
 };
 
 // Registry of compiled pass kernels (one table per instantiation unit).
 const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec = 0,
-                               int logx = 0);
+                               int logx = 0, int pipe = 0);
+// first pipelined single-pass kernel registered for (log2 L, layout), or NULL
+const KernelEntry *find_pipe_rows(int logl, int lay);
 int kernel_count();
 const KernelEntry *kernel_at(int i);
 

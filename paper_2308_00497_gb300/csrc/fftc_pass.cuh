@@ -33,8 +33,11 @@
 
 namespace fftc {
 
+// Line pitch in float2 words: odd for 16-line tiles (their c-fast accesses then hit 16
+// distinct banks), +2 otherwise so that every line slot starts 16-byte aligned (a bulk
+// copy destination) while the 8-line c-fast accesses stay conflict-free.
 __host__ __device__ constexpr int pass_pitch(int line_words, int lines) {
-    return lines == 1 ? line_words : line_words + (lines == 8 ? 2 : 1);
+    return lines == 1 ? line_words : line_words + (lines >= 16 ? 1 : 2);
 }
 
 template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0>
@@ -42,6 +45,7 @@ struct Pass {
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
     static constexpr int NT = C * TPL;
+    static constexpr int C_LINES = C, LIN_LAYOUT = LIN;
     static constexpr int LINE_WORDS = L + (L >> LOGE);
     static constexpr int PITCH = pass_pitch(LINE_WORDS, C);
     static constexpr int SMEM = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
@@ -165,7 +169,31 @@ struct Pass {
         }
     }
 
-    template <int s>
+    // stage-0 operands from a landing buffer filled by the bulk copy engine: each line
+    // occupies its own PITCH slot, interleaved as float2 or split as L reals then L imaginaries
+    template <int R>
+    __device__ __forceinline__ static void load_landed(const PassParams &p, float2 (&v)[E], const float2 *line, int tau,
+                                                       int64_t g) {
+        const int cj = conj_of(p, g, p.conj_in);
+#pragma unroll
+        for (int q = 0; q < E / R; ++q) {
+            const int j = tau + q * TPL;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                float2 x;
+                if constexpr (LIN == LAYOUT_IL) {
+                    x = line[j + t * (L / R)];
+                } else {
+                    const float *lf = reinterpret_cast<const float *>(line);
+                    x = make_float2(lf[j + t * (L / R)], lf[L + j + t * (L / R)]);
+                }
+                if (cj) x.y = -x.y;
+                v[q * R + t] = x;
+            }
+        }
+    }
+
+    template <int s, bool LANDED = false>
     __device__ __forceinline__ static void stage(const PassParams &p, float2 *sm, float2 (&v)[E], int tid, int64_t g0) {
         constexpr int LR = Sc::lr(s), R = 1 << LR, LNS = Sc::lns(s), NS = 1 << LNS;
         constexpr bool TF = tau_fast(s);
@@ -176,7 +204,8 @@ struct Pass {
         float2 *line = sm + c * PITCH;
 
         if constexpr (s == 0) {
-            load_global<R>(p, v, tau, g, live);
+            if constexpr (LANDED) load_landed<R>(p, v, line, tau, g);
+            else load_global<R>(p, v, tau, g, live);
         } else {
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
@@ -203,7 +232,7 @@ struct Pass {
         for (int q = 0; q < E / R; ++q) dft<R>(v + q * R);
 
         if constexpr (s < S - 1) {
-            if constexpr (s > 0) sync();  // every read of this stage precedes any overwrite
+            if constexpr (s > 0 || LANDED) sync();  // every read of this stage precedes any overwrite
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
                 const int j = tau + q * TPL;
@@ -218,7 +247,7 @@ struct Pass {
                 }
             }
             sync();
-            stage<s + 1>(p, sm, v, tid, g0);
+            stage<s + 1, LANDED>(p, sm, v, tid, g0);
         } else {
             store_global<R>(p, v, tau, g, live);
         }
@@ -234,6 +263,12 @@ struct Pass {
     __device__ __forceinline__ static void run_tile(const PassParams &p, int64_t tile, float2 *sm) {
         float2 v[E];
         stage<0>(p, sm, v, threadIdx.x, tile * C);
+    }
+
+    // one tile whose input lines already sit in `sm` (line c at c * PITCH)
+    __device__ __forceinline__ static void run_tile_landed(const PassParams &p, int64_t tile, float2 *sm) {
+        float2 v[E];
+        stage<0, true>(p, sm, v, threadIdx.x, tile * C);
     }
 };
 
@@ -276,7 +311,8 @@ constexpr KernelEntry entry() {
                        &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
                        &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
                        0,
-                       LOGX};
+                       LOGX,
+                       0};
 }
 
 }  // namespace fftc

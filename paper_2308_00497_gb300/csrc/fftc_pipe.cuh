@@ -1,0 +1,186 @@
+// Pipelined persistent single-pass kernel: the bulk-copy (TMA) engine streams whole
+// tiles into shared memory while the CTA transforms the previous tile.
+//
+// Each CTA owns NBUF landing buffers, each with one mbarrier. Tile k of a CTA goes to
+// buffer k mod NBUF; thread 0 arms the barrier with the expected byte count and issues
+// one cp.async.bulk per line (two per line for the split layout) into that line's PITCH
+// slot. The CTA waits on the barrier (bounded: an expired wait sets the plan's error word,
+// waits a bounded time for its own copies still in flight, and returns), transforms the
+// tile with stage 0 reading the landed data and the exchanges reusing the same buffer,
+// writes the result to HBM from registers, and only then refills the buffer with tile
+// k + NBUF. So NBUF - 1 tiles of HBM reads are always in flight behind the compute.
+#pragma once
+
+#include "fftc_pass.cuh"
+
+namespace fftc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// order this thread's earlier generic-proxy shared accesses before later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase with the given parity: gives up after `limit` polls or
+// kMbarWaitNs nanoseconds, whichever comes first
+constexpr uint64_t kMbarWaitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    const uint64_t t0 = global_ns();
+    for (long long i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && global_ns() - t0 > kMbarWaitNs) return false;
+    }
+    return false;
+}
+
+constexpr long long kMbarSpinLimit = 1ll << 24;
+
+template <class P, int NBUF>
+struct PipeRows {
+    static_assert(P::S > 1, "pipelined tiles need an exchange buffer");
+    static constexpr int BUF_WORDS = P::C_LINES * P::PITCH;  // float2 per buffer
+    static constexpr int SMEM = NBUF * BUF_WORDS * (int)sizeof(float2);
+    static constexpr int NT = P::NT;
+
+    // thread 0: arm `bar` and copy the live lines of `tile` into `buf`
+    __device__ __forceinline__ static void issue(const PassParams &p, int64_t tile, float2 *buf, uint64_t *bar) {
+        const int64_t g0 = tile * P::C_LINES;
+        const int64_t left = p.total_lines - g0;
+        const int nl = left < P::C_LINES ? (int)left : P::C_LINES;
+        constexpr uint32_t line_bytes = P::L * sizeof(float2);
+        mbar_arrive_expect_tx(bar, line_bytes * nl);
+        for (int c = 0; c < nl; ++c) {
+            const int64_t off = (g0 + c) * p.in_tr;  // contiguous lines (single pass)
+            float2 *dst = buf + c * P::PITCH;
+            if constexpr (P::LIN_LAYOUT == LAYOUT_IL) {
+                bulk_g2s(dst, reinterpret_cast<const float2 *>(p.in) + off, line_bytes, bar);
+            } else {
+                float *df = reinterpret_cast<float *>(dst);
+                bulk_g2s(df, p.in + off, line_bytes / 2, bar);
+                bulk_g2s(df + P::L, p.in + p.in_plane + off, line_bytes / 2, bar);
+            }
+        }
+    }
+
+    __device__ static void run(const PassParams &p) {
+        extern __shared__ __align__(128) unsigned char pipe_raw[];
+        float2 *bufs = reinterpret_cast<float2 *>(pipe_raw);
+        __shared__ __align__(8) uint64_t bars[NBUF];
+        const int64_t ntiles = (p.total_lines + P::C_LINES - 1) / P::C_LINES;
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int b = 0; b < NBUF; ++b) {
+                const int64_t t = blockIdx.x + (int64_t)b * gridDim.x;
+                if (t < ntiles) issue(p, t, bufs + b * BUF_WORDS, &bars[b]);
+            }
+        for (int64_t k = 0;; ++k) {
+            const int64_t tile = blockIdx.x + k * gridDim.x;
+            if (tile >= ntiles) break;
+            const int b = (int)(k % NBUF);
+            const uint32_t parity = (uint32_t)((k / NBUF) & 1);
+            if (!mbar_wait_bounded(&bars[b], parity, kMbarSpinLimit)) {
+                if (threadIdx.x == 0 && p.err) atomicExch(p.err, 2);
+                // let this CTA's other copies land before the shared memory goes away
+                for (int d = 1; d < NBUF; ++d) {
+                    const int64_t kk = k + d;
+                    if (blockIdx.x + kk * gridDim.x < ntiles)
+                        mbar_wait_bounded(&bars[kk % NBUF], (uint32_t)((kk / NBUF) & 1), kMbarSpinLimit);
+                }
+                return;
+            }
+            P::run_tile_landed(p, tile, bufs + b * BUF_WORDS);
+            __syncthreads();  // every shared read of buffer b is done
+            const int64_t next = tile + (int64_t)NBUF * gridDim.x;
+            if (threadIdx.x == 0 && next < ntiles) {
+                fence_proxy_async_smem();
+                issue(p, next, bufs + b * BUF_WORDS, &bars[b]);
+            }
+        }
+    }
+};
+
+template <class P, int NBUF>
+__global__ void __launch_bounds__(P::NT, P::MINB) k_pipe_rows(const __grid_constant__ PassParams p) {
+    PipeRows<P, NBUF>::run(p);
+}
+
+template <class P, int NBUF>
+struct PipeLauncher {
+    static int &grid_cache() {
+        static int g = 0;
+        return g;
+    }
+    static cudaError_t prepare() {
+        using PR = PipeRows<P, NBUF>;
+        cudaError_t e = cudaFuncSetAttribute(k_pipe_rows<P, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0, dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipe_rows<P, NBUF>, PR::NT, PR::SMEM)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        grid_cache() = (per_sm > 0 ? per_sm : 1) * sms;
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const PassParams &p, cudaStream_t st) {
+        using PR = PipeRows<P, NBUF>;
+        const int64_t ntiles = (p.total_lines + P::C_LINES - 1) / P::C_LINES;
+        if (ntiles <= 0) return cudaSuccess;
+        if (grid_cache() == 0) {
+            cudaError_t e = prepare();
+            if (e != cudaSuccess) return e;
+        }
+        const int grid = (int)(ntiles < grid_cache() ? ntiles : grid_cache());
+        k_pipe_rows<P, NBUF><<<grid, PR::NT, PR::SMEM, st>>>(p);
+        return cudaGetLastError();
+    }
+};
+
+// registry entry of a pipelined single-pass kernel (kind KIND_ROWS, lines = C; `pipe` = NBUF)
+template <int LOGL, int LOGE, int C, int LAY, int NBUF>
+constexpr KernelEntry pipe_entry() {
+    using P = Pass<LOGL, LOGE, C, KIND_ROWS, LAY, LAY>;
+    using L = PipeLauncher<P, NBUF>;
+    return KernelEntry{KIND_ROWS, LOGL, LOGE, C, LAY, LAY, P::NT, PipeRows<P, NBUF>::SMEM, &L::launch, &L::prepare, 0,
+                       0,         NBUF};
+}
+
+}  // namespace fftc

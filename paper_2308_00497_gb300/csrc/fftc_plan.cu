@@ -104,8 +104,24 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         }
         pp.lin = pp.lout = lay;
         pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay, prec);
+        if (!tc && env_int("FFTC_PIPE", 1)) {  // pipelined persistent kernel when one exists for this size
+            const int pe = env_int("FFTC_TUNE_PIPE_E", 0), pc = env_int("FFTC_TUNE_PIPE_C", 0);
+            const KernelEntry *k = find_pipe_rows(pp.logl, lay);
+            for (int i = 0; pe && i < kernel_count(); ++i) {
+                const KernelEntry *e = kernel_at(i);
+                if (e->pipe && e->kind == KIND_ROWS && e->logl == pp.logl && e->lin == lay && e->loge == pe &&
+                    (!pc || e->lines == pc))
+                    k = e;
+            }
+            if (k) {
+                pp.k = k;
+                pp.loge = k->loge;
+                pp.lines = k->lines;
+            }
+        }
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
         b.in_plane = b.out_plane = plane;
         b.total_lines = B;
         b.log_lpt = 0;

@@ -4,8 +4,8 @@
 namespace fftc {
 
 extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
-    kTcBf16Table[];
-extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count;
+    kTcBf16Table[], kPipeTable[];
+extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count, kPipeCount;
 
 struct TableRef {
     const KernelEntry *t;
@@ -14,7 +14,7 @@ struct TableRef {
 static const TableRef kTables[] = {
     {kRowsIlTable, &kRowsIlCount}, {kRowsSplitTable, &kRowsSplitCount},
     {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
-    {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
+    {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count}, {kPipeTable, &kPipeCount},
 };
 
 int kernel_count() {

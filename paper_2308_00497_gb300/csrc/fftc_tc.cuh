@@ -282,7 +282,7 @@ template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
 constexpr KernelEntry tc_entry() {
     using P = TcPass<LOGL, C, KIND, LIN, LOUT, PREC>;
     return KernelEntry{KIND,   LOGL,   4, C, LIN, LOUT, P::NT, P::SMEM, &launch_tc<LOGL, C, KIND, LIN, LOUT, PREC>,
-                       &prepare_tc<LOGL, C, KIND, LIN, LOUT, PREC>, PREC, 0};
+                       &prepare_tc<LOGL, C, KIND, LIN, LOUT, PREC>, PREC, 0, 0};
 }
 
 }  // namespace fftc
