@@ -45,7 +45,7 @@ struct Pass {
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
     static constexpr int NT = C * TPL;
-    static constexpr int C_LINES = C, LIN_LAYOUT = LIN;
+    static constexpr int C_LINES = C, LIN_LAYOUT = LIN, KIND_ID = KIND;
     static constexpr int LINE_WORDS = L + (L >> LOGE);
     static constexpr int PITCH = pass_pitch(LINE_WORDS, C);
     static constexpr int SMEM = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
@@ -169,24 +169,36 @@ struct Pass {
         }
     }
 
-    // stage-0 operands from a landing buffer filled by the bulk copy engine: each line
-    // occupies its own PITCH slot, interleaved as float2 or split as L reals then L imaginaries
+    // Stage-0 operands from a landing buffer filled by the bulk-copy (TMA) engine:
+    //   single pass (contiguous lines, one copy per line): line c in its PITCH slot,
+    //     interleaved, or split as L reals then L imaginaries;
+    //   pass 2 (C consecutive workspace rows, one copy per tile): row-major [c][a];
+    //   pass 1 (a 2D tensor box of C columns x L rows): column-major [a][c], split as
+    //     the real box then the imaginary box.
+    __device__ __forceinline__ static float2 landed(const float2 *sm, int c, int a) {
+        if constexpr (KIND == KIND_ROWS) {
+            if constexpr (LIN == LAYOUT_IL) return sm[c * PITCH + a];
+            const float *lf = reinterpret_cast<const float *>(sm + c * PITCH);
+            return make_float2(lf[a], lf[L + a]);
+        } else if constexpr (KIND == KIND_ROWST) {
+            return sm[c * L + a];
+        } else {
+            if constexpr (LIN == LAYOUT_IL) return sm[a * C + c];
+            const float *lf = reinterpret_cast<const float *>(sm);
+            return make_float2(lf[a * C + c], lf[L * C + a * C + c]);
+        }
+    }
+
     template <int R>
-    __device__ __forceinline__ static void load_landed(const PassParams &p, float2 (&v)[E], const float2 *line, int tau,
-                                                       int64_t g) {
+    __device__ __forceinline__ static void load_landed(const PassParams &p, float2 (&v)[E], const float2 *sm, int c,
+                                                       int tau, int64_t g) {
         const int cj = conj_of(p, g, p.conj_in);
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
             const int j = tau + q * TPL;
 #pragma unroll
             for (int t = 0; t < R; ++t) {
-                float2 x;
-                if constexpr (LIN == LAYOUT_IL) {
-                    x = line[j + t * (L / R)];
-                } else {
-                    const float *lf = reinterpret_cast<const float *>(line);
-                    x = make_float2(lf[j + t * (L / R)], lf[L + j + t * (L / R)]);
-                }
+                float2 x = landed(sm, c, j + t * (L / R));
                 if (cj) x.y = -x.y;
                 v[q * R + t] = x;
             }
@@ -204,7 +216,7 @@ struct Pass {
         float2 *line = sm + c * PITCH;
 
         if constexpr (s == 0) {
-            if constexpr (LANDED) load_landed<R>(p, v, line, tau, g);
+            if constexpr (LANDED) load_landed<R>(p, v, sm, c, tau, g);
             else load_global<R>(p, v, tau, g, live);
         } else {
 #pragma unroll

@@ -1,15 +1,21 @@
-// Pipelined persistent single-pass kernel: the bulk-copy (TMA) engine streams whole
-// tiles into shared memory while the CTA transforms the previous tile.
+// Pipelined persistent pass kernels: the bulk-copy (TMA) engine streams whole tiles
+// into shared memory while the CTA transforms the previous tile.
 //
 // Each CTA owns NBUF landing buffers, each with one mbarrier. Tile k of a CTA goes to
 // buffer k mod NBUF; thread 0 arms the barrier with the expected byte count and issues
-// one cp.async.bulk per line (two per line for the split layout) into that line's PITCH
-// slot. The CTA waits on the barrier (bounded: an expired wait sets the plan's error word,
+// the copies:
+//   single pass:  one cp.async.bulk per line (two per line for the split layout);
+//   four-step 2:  one cp.async.bulk for the tile's C consecutive workspace rows;
+//   four-step 1:  cp.async.bulk.tensor.2d boxes of C columns x up to 256 rows through a
+//                 tensor map of the input (one map per plane in the split layout).
+// The CTA waits on the barrier (bounded: an expired wait sets the plan's error word,
 // waits a bounded time for its own copies still in flight, and returns), transforms the
 // tile with stage 0 reading the landed data and the exchanges reusing the same buffer,
 // writes the result to HBM from registers, and only then refills the buffer with tile
-// k + NBUF. So NBUF - 1 tiles of HBM reads are always in flight behind the compute.
+// k + NBUF. So NBUF - 1 tiles of HBM reads are in flight behind the compute.
 #pragma once
+
+#include <cuda.h>
 
 #include "fftc_pass.cuh"
 
@@ -36,6 +42,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// 2D tensor box -> shared (128-byte aligned destination; x * element size a multiple of 16)
+__device__ __forceinline__ void tensor2d_g2s(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -68,38 +83,72 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr long long kMbarSpinLimit = 1ll << 24;
 
-template <class P, int NBUF>
-struct PipeRows {
-    static_assert(P::S > 1, "pipelined tiles need an exchange buffer");
-    static constexpr int BUF_WORDS = P::C_LINES * P::PITCH;  // float2 per buffer
-    static constexpr int SMEM = NBUF * BUF_WORDS * (int)sizeof(float2);
-    static constexpr int NT = P::NT;
+struct PipeArgs {
+    PassParams p;
+    CUtensorMap tm[2];  // four-step pass 1: input (real plane / interleaved) and imaginary plane
+};
 
-    // thread 0: arm `bar` and copy the live lines of `tile` into `buf`
-    __device__ __forceinline__ static void issue(const PassParams &p, int64_t tile, float2 *buf, uint64_t *bar) {
-        const int64_t g0 = tile * P::C_LINES;
-        const int64_t left = p.total_lines - g0;
-        const int nl = left < P::C_LINES ? (int)left : P::C_LINES;
-        constexpr uint32_t line_bytes = P::L * sizeof(float2);
-        mbar_arrive_expect_tx(bar, line_bytes * nl);
-        for (int c = 0; c < nl; ++c) {
-            const int64_t off = (g0 + c) * p.in_tr;  // contiguous lines (single pass)
-            float2 *dst = buf + c * P::PITCH;
-            if constexpr (P::LIN_LAYOUT == LAYOUT_IL) {
-                bulk_g2s(dst, reinterpret_cast<const float2 *>(p.in) + off, line_bytes, bar);
-            } else {
-                float *df = reinterpret_cast<float *>(dst);
-                bulk_g2s(df, p.in + off, line_bytes / 2, bar);
-                bulk_g2s(df + P::L, p.in + p.in_plane + off, line_bytes / 2, bar);
+template <class P, int NBUF>
+struct PipeTile {
+    static_assert(P::S > 1, "pipelined tiles need an exchange buffer");
+    static constexpr int KIND = P::KIND_ID;
+    static constexpr int C = P::C_LINES, L = P::L;
+    static constexpr int RAW_WORDS = C * P::PITCH > C * L ? C * P::PITCH : C * L;
+    static constexpr int BUF_WORDS = (RAW_WORDS + 15) / 16 * 16;  // 128-byte multiple
+    static constexpr int SMEM = NBUF * BUF_WORDS * (int)sizeof(float2) + 128;  // + room to align the base
+    static constexpr int NT = P::NT;
+    static constexpr int BOXR = L < 256 ? L : 256;  // rows per tensor box (box dims <= 256)
+
+    // thread 0: arm `bar` and start the copies of `tile` into `buf`
+    __device__ __forceinline__ static void issue(const PipeArgs &a, int64_t tile, float2 *buf, uint64_t *bar) {
+        const PassParams &p = a.p;
+        const int64_t g0 = tile * C;
+        if constexpr (KIND == KIND_COLS) {
+            const int tr = (int)(g0 >> p.log_lpt), b0 = (int)(g0 & ((int64_t(1) << p.log_lpt) - 1));
+            mbar_arrive_expect_tx(bar, (uint32_t)(L * C * sizeof(float2)));
+#pragma unroll
+            for (int k = 0; k < L / BOXR; ++k) {
+                const int y = tr * L + k * BOXR;
+                if constexpr (P::LIN_LAYOUT == LAYOUT_IL) {
+                    tensor2d_g2s(buf + k * BOXR * C, &a.tm[0], b0, y, bar);
+                } else {
+                    float *bf = reinterpret_cast<float *>(buf);
+                    tensor2d_g2s(bf + k * BOXR * C, &a.tm[0], b0, y, bar);
+                    tensor2d_g2s(bf + L * C + k * BOXR * C, &a.tm[1], b0, y, bar);
+                }
+            }
+        } else if constexpr (KIND == KIND_ROWST) {
+            // C consecutive rows of one transform are contiguous in the workspace
+            const int64_t off = (g0 >> p.log_lpt) * p.in_tr + (g0 & ((int64_t(1) << p.log_lpt) - 1)) * p.in_line;
+            constexpr uint32_t bytes = (uint32_t)(C * L * sizeof(float2));
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(buf, reinterpret_cast<const float2 *>(p.in) + off, bytes, bar);
+        } else {
+            const int64_t left = p.total_lines - g0;
+            const int nl = left < C ? (int)left : C;
+            constexpr uint32_t line_bytes = L * sizeof(float2);
+            mbar_arrive_expect_tx(bar, line_bytes * nl);
+            for (int c = 0; c < nl; ++c) {
+                const int64_t off = (g0 + c) * p.in_tr;  // contiguous lines
+                float2 *dst = buf + c * P::PITCH;
+                if constexpr (P::LIN_LAYOUT == LAYOUT_IL) {
+                    bulk_g2s(dst, reinterpret_cast<const float2 *>(p.in) + off, line_bytes, bar);
+                } else {
+                    float *df = reinterpret_cast<float *>(dst);
+                    bulk_g2s(df, p.in + off, line_bytes / 2, bar);
+                    bulk_g2s(df + L, p.in + p.in_plane + off, line_bytes / 2, bar);
+                }
             }
         }
     }
 
-    __device__ static void run(const PassParams &p) {
+    __device__ static void run(const PipeArgs &a) {
+        const PassParams &p = a.p;
         extern __shared__ __align__(128) unsigned char pipe_raw[];
-        float2 *bufs = reinterpret_cast<float2 *>(pipe_raw);
+        // tensor-copy destinations must be 128-byte aligned
+        float2 *bufs = reinterpret_cast<float2 *>(pipe_raw + ((128 - (smem_u32(pipe_raw) & 127)) & 127));
         __shared__ __align__(8) uint64_t bars[NBUF];
-        const int64_t ntiles = (p.total_lines + P::C_LINES - 1) / P::C_LINES;
+        const int64_t ntiles = (p.total_lines + C - 1) / C;
         if (threadIdx.x == 0) {
             for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
             fence_mbar_init();
@@ -108,7 +157,7 @@ struct PipeRows {
         if (threadIdx.x == 0)
             for (int b = 0; b < NBUF; ++b) {
                 const int64_t t = blockIdx.x + (int64_t)b * gridDim.x;
-                if (t < ntiles) issue(p, t, bufs + b * BUF_WORDS, &bars[b]);
+                if (t < ntiles) issue(a, t, bufs + b * BUF_WORDS, &bars[b]);
             }
         for (int64_t k = 0;; ++k) {
             const int64_t tile = blockIdx.x + k * gridDim.x;
@@ -130,16 +179,19 @@ struct PipeRows {
             const int64_t next = tile + (int64_t)NBUF * gridDim.x;
             if (threadIdx.x == 0 && next < ntiles) {
                 fence_proxy_async_smem();
-                issue(p, next, bufs + b * BUF_WORDS, &bars[b]);
+                issue(a, next, bufs + b * BUF_WORDS, &bars[b]);
             }
         }
     }
 };
 
 template <class P, int NBUF>
-__global__ void __launch_bounds__(P::NT, P::MINB) k_pipe_rows(const __grid_constant__ PassParams p) {
-    PipeRows<P, NBUF>::run(p);
+__global__ void __launch_bounds__(P::NT, P::MINB) k_pipe(const __grid_constant__ PipeArgs a) {
+    PipeTile<P, NBUF>::run(a);
 }
+
+// host: encode the tensor map(s) of a four-step pass-1 input (see PipeTile::issue)
+bool encode_cols_maps(const PassParams &p, int logl, int lines, int lay, CUtensorMap *tm);
 
 template <class P, int NBUF>
 struct PipeLauncher {
@@ -148,12 +200,12 @@ struct PipeLauncher {
         return g;
     }
     static cudaError_t prepare() {
-        using PR = PipeRows<P, NBUF>;
-        cudaError_t e = cudaFuncSetAttribute(k_pipe_rows<P, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, PR::SMEM);
+        using PT = PipeTile<P, NBUF>;
+        cudaError_t e = cudaFuncSetAttribute(k_pipe<P, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0, dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipe_rows<P, NBUF>, PR::NT, PR::SMEM)) !=
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipe<P, NBUF>, PT::NT, PT::SMEM)) !=
             cudaSuccess)
             return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -161,26 +213,32 @@ struct PipeLauncher {
         return cudaSuccess;
     }
     static cudaError_t launch(const PassParams &p, cudaStream_t st) {
-        using PR = PipeRows<P, NBUF>;
-        const int64_t ntiles = (p.total_lines + P::C_LINES - 1) / P::C_LINES;
+        using PT = PipeTile<P, NBUF>;
+        const int64_t ntiles = (p.total_lines + PT::C - 1) / PT::C;
         if (ntiles <= 0) return cudaSuccess;
         if (grid_cache() == 0) {
             cudaError_t e = prepare();
             if (e != cudaSuccess) return e;
         }
+        PipeArgs a;
+        memset(&a, 0, sizeof(a));
+        a.p = p;
+        if constexpr (PT::KIND == KIND_COLS)
+            if (!encode_cols_maps(p, P::L == 0 ? 0 : __builtin_ctz(P::L), PT::C, P::LIN_LAYOUT, a.tm))
+                return cudaErrorInvalidValue;
         const int grid = (int)(ntiles < grid_cache() ? ntiles : grid_cache());
-        k_pipe_rows<P, NBUF><<<grid, PR::NT, PR::SMEM, st>>>(p);
+        k_pipe<P, NBUF><<<grid, PT::NT, PT::SMEM, st>>>(a);
         return cudaGetLastError();
     }
 };
 
-// registry entry of a pipelined single-pass kernel (kind KIND_ROWS, lines = C; `pipe` = NBUF)
-template <int LOGL, int LOGE, int C, int LAY, int NBUF>
+// registry entry of a pipelined pass kernel (`pipe` = NBUF)
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int NBUF>
 constexpr KernelEntry pipe_entry() {
-    using P = Pass<LOGL, LOGE, C, KIND_ROWS, LAY, LAY>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
     using L = PipeLauncher<P, NBUF>;
-    return KernelEntry{KIND_ROWS, LOGL, LOGE, C, LAY, LAY, P::NT, PipeRows<P, NBUF>::SMEM, &L::launch, &L::prepare, 0,
-                       0,         NBUF};
+    return KernelEntry{KIND, LOGL, LOGE, C, LIN, LOUT, P::NT, PipeTile<P, NBUF>::SMEM, &L::launch, &L::prepare, 0,
+                       LOGX, NBUF};
 }
 
 }  // namespace fftc

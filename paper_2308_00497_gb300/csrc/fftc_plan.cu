@@ -104,7 +104,9 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         }
         pp.lin = pp.lout = lay;
         pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay, prec);
-        if (!tc && env_int("FFTC_PIPE", 1)) {  // pipelined persistent kernel when one exists for this size
+        // pipelined persistent kernel where it measured faster (n = 2^9 .. 2^11, 2^13)
+        const bool pipe_dflt = p->logn == 9 || p->logn == 10 || p->logn == 11 || p->logn == 13;
+        if (!tc && env_int("FFTC_PIPE", pipe_dflt ? 1 : 0)) {
             const int pe = env_int("FFTC_TUNE_PIPE_E", 0), pc = env_int("FFTC_TUNE_PIPE_C", 0);
             const KernelEntry *k = find_pipe_rows(pp.logl, lay);
             for (int i = 0; pe && i < kernel_count(); ++i) {
@@ -191,10 +193,14 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lines = c1;
         pp.lin = lay;
         pp.lout = LAYOUT_IL;
-        pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
+        pp.k = nullptr;
+        if (!tc && env_int("FFTC_PIPE4", 1))  // pipelined (tensor-map fed) pass when compiled
+            pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk, 2);
+        if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
         b.in_plane = plane;
         b.out_plane = 0;
         b.total_lines = B * K;
@@ -222,10 +228,14 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lines = c2;
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
-        pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
+        pp.k = nullptr;
+        if (!tc && env_int("FFTC_PIPE4", 1))
+            pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm, 2);
+        if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
         b.in_plane = 0;
         b.out_plane = plane;
         b.total_lines = B * M;
