@@ -194,7 +194,9 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lin = lay;
         pp.lout = LAYOUT_IL;
         pp.k = nullptr;
-        if (!tc && env_int("FFTC_PIPE4", 1))  // pipelined (tensor-map fed) pass when compiled
+        // pipelined (tensor-map fed) pass: off by default, the narrow column boxes make the
+        // bulk-copy engine issue one small request per row (FFTC_PIPE4=1 enables it)
+        if (!tc && env_int("FFTC_PIPE4", 0))
             pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk, 2);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
@@ -229,7 +231,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
         pp.k = nullptr;
-        if (!tc && env_int("FFTC_PIPE4", 1))
+        if (!tc && env_int("FFTC_PIPE4", 0))
             pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm, 2);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);

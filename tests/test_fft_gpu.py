@@ -188,3 +188,40 @@ def test_l2_resident_matches_two_launch_path(monkeypatch, e):
     torch.cuda.synchronize()
     err = rel_l2_rows(a.cpu().numpy(), b.cpu().numpy().astype(np.complex128))
     assert err.max() <= 2 * tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [14, 17, 20])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_tensor_map_fed_four_step(monkeypatch, e, layout):
+    """The bulk-copy / tensor-map fed four-step passes (opt-in) against the oracle."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_PIPE4", "1")
+    n = 1 << e
+    B = max(2, (1 << 21) // n)
+    x = si.uniform_complex(B, n, seed=e + 5)
+    p = fc.Plan(n, B, layout, e % 2 == 1)
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    rows = np.array([0, B - 1])
+    ref = oracle.fft(x[rows].astype(np.complex128), inverse=e % 2 == 1)
+    assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [9, 10, 11, 12, 13])
+@pytest.mark.parametrize("pipe", ["0", "1"])
+def test_single_pass_both_kernels(monkeypatch, e, pipe):
+    """Single-pass sizes through the bulk-copy fed persistent kernel and the plain one."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_PIPE", pipe)
+    n = 1 << e
+    B = 1000 + e  # not a multiple of any tile: the last tile is partial
+    x = si.uniform_complex(B, n, seed=e)
+    for layout in ("interleaved", "split"):
+        p = fc.Plan(n, B, layout, False)
+        y = from_device(p.execute(to_device(x, layout)), layout)
+        torch.cuda.synchronize()
+        p.check()
+        rows = np.array([0, 1, B // 2, B - 1])
+        ref = oracle.fft(x[rows].astype(np.complex128))
+        assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
