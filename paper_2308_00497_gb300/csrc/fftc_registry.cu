@@ -4,8 +4,9 @@
 namespace fftc {
 
 extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
-    kTcBf16Table[], kPipeTable[];
-extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count, kPipeCount;
+    kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[];
+extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count,
+    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count;
 
 struct TableRef {
     const KernelEntry *t;
@@ -14,7 +15,8 @@ struct TableRef {
 static const TableRef kTables[] = {
     {kRowsIlTable, &kRowsIlCount}, {kRowsSplitTable, &kRowsSplitCount},
     {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
-    {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count}, {kPipeTable, &kPipeCount},
+    {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
+    {kPipeRowsIlTable, &kPipeRowsIlCount}, {kPipeRowsSplitTable, &kPipeRowsSplitCount}, {kPipe4Table, &kPipe4Count},
 };
 
 int kernel_count() {

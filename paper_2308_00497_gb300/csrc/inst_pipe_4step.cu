@@ -1,16 +1,12 @@
-// Instantiations of the pipelined persistent pass kernels (bulk-copy landing buffers,
-// fftc_pipe.cuh): single pass for n = 2^8 .. 2^13, and both four-step passes for
-// n = 2^14 .. 2^20 with compile-time strides, both layouts. The first single-pass entry
-// of each size is its default; the others are tuning alternatives.
+// Instantiations of the pipelined persistent four-step passes (pass 1 fed by 2D tensor
+// maps, pass 2 by one bulk copy per tile; fftc_pipe.cuh) for n = 2^14 .. 2^20 with
+// compile-time strides, both layouts, and the host encoder of the pass-1 tensor maps.
 #include <cstring>
 
 #include "fftc_pipe.cuh"
 
 namespace fftc {
 
-#define PR2(LOGL, LOGE, C, NBUF)                                                \
-    pipe_entry<LOGL, LOGE, C, KIND_ROWS, LAYOUT_IL, LAYOUT_IL, 0, NBUF>(),      \
-        pipe_entry<LOGL, LOGE, C, KIND_ROWS, LAYOUT_SPLIT, LAYOUT_SPLIT, 0, NBUF>()
 #define PC2(LOGL, LOGE, C, LOGX, NBUF)                                          \
     pipe_entry<LOGL, LOGE, C, KIND_COLS, LAYOUT_IL, LAYOUT_IL, LOGX, NBUF>(),   \
         pipe_entry<LOGL, LOGE, C, KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL, LOGX, NBUF>()
@@ -18,17 +14,13 @@ namespace fftc {
     pipe_entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_IL, LOGX, NBUF>(),  \
         pipe_entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT, LOGX, NBUF>()
 
-extern const KernelEntry kPipeTable[] = {
-    PR2(8, 4, 8, 3),  PR2(9, 5, 8, 2),  PR2(10, 5, 4, 2), PR2(11, 5, 2, 2), PR2(12, 4, 1, 2), PR2(13, 5, 1, 2),
-    // alternatives
-    PR2(9, 4, 4, 3),  PR2(10, 5, 8, 2), PR2(11, 4, 2, 2), PR2(12, 5, 1, 2), PR2(13, 4, 1, 2),
-    // four-step passes, n = 2^14 .. 2^20 (same radix choices as the two-launch path)
+extern const KernelEntry kPipe4Table[] = {
     PC2(7, 4, 16, 7, 2), PC2(7, 4, 16, 8, 2), PC2(8, 4, 16, 8, 2), PC2(8, 4, 16, 9, 2), PC2(9, 5, 8, 9, 2),
     PC2(9, 5, 8, 10, 2), PC2(10, 5, 8, 10, 2),
     PT2(7, 4, 16, 7, 2), PT2(8, 4, 16, 7, 2), PT2(8, 4, 16, 8, 2), PT2(9, 5, 8, 8, 2), PT2(9, 5, 8, 9, 2),
     PT2(10, 5, 8, 9, 2), PT2(10, 5, 8, 10, 2),
 };
-extern const int kPipeCount = sizeof(kPipeTable) / sizeof(kPipeTable[0]);
+extern const int kPipe4Count = sizeof(kPipe4Table) / sizeof(kPipe4Table[0]);
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
