@@ -31,34 +31,44 @@
 
 namespace fftc {
 
-// (id, LOGL, LOGE, C, KIND, IDX): every branch has C * 2^(LOGL - LOGE) = 256 threads
-#define FFTC_UNEVEN_BRANCHES(X)            \
-    X(0, 6, 4, 64, KIND_ROWS, true)        \
-    X(1, 7, 4, 32, KIND_ROWS, true)        \
-    X(2, 8, 4, 16, KIND_ROWS, true)        \
-    X(3, 9, 4, 8, KIND_ROWS, true)         \
-    X(4, 10, 4, 4, KIND_ROWS, true)        \
-    X(5, 11, 4, 2, KIND_ROWS, true)        \
-    X(6, 12, 4, 1, KIND_ROWS, true)        \
-    X(7, 6, 2, 16, KIND_COLS, false)       \
-    X(8, 7, 3, 16, KIND_COLS, false)       \
-    X(9, 8, 4, 16, KIND_COLS, false)       \
-    X(10, 6, 2, 16, KIND_ROWST, false)     \
-    X(11, 7, 3, 16, KIND_ROWST, false)     \
-    X(12, 8, 4, 16, KIND_ROWST, false)
+// (id, LOGL, LOGE, C, KIND, IDX, LOGX): every branch has C * 2^(LOGL - LOGE) = 256
+// threads; the four-step branches carry their element stride 2^LOGX at compile time
+// (one pair per split n = M K of the classes 2^13 .. 2^16).
+#define FFTC_UNEVEN_BRANCHES(X)                \
+    X(0, 6, 4, 64, KIND_ROWS, true, 0)         \
+    X(1, 7, 4, 32, KIND_ROWS, true, 0)         \
+    X(2, 8, 4, 16, KIND_ROWS, true, 0)         \
+    X(3, 9, 4, 8, KIND_ROWS, true, 0)          \
+    X(4, 10, 4, 4, KIND_ROWS, true, 0)         \
+    X(5, 11, 4, 2, KIND_ROWS, true, 0)         \
+    X(6, 12, 4, 1, KIND_ROWS, true, 0)         \
+    X(7, 6, 2, 16, KIND_COLS, false, 7)        \
+    X(8, 7, 3, 16, KIND_COLS, false, 6)        \
+    X(9, 7, 3, 16, KIND_COLS, false, 7)        \
+    X(10, 7, 3, 16, KIND_COLS, false, 8)       \
+    X(11, 8, 4, 16, KIND_COLS, false, 7)       \
+    X(12, 8, 4, 16, KIND_COLS, false, 8)       \
+    X(13, 7, 3, 16, KIND_ROWST, false, 6)      \
+    X(14, 6, 2, 16, KIND_ROWST, false, 7)      \
+    X(15, 7, 3, 16, KIND_ROWST, false, 7)      \
+    X(16, 8, 4, 16, KIND_ROWST, false, 7)      \
+    X(17, 7, 3, 16, KIND_ROWST, false, 8)      \
+    X(18, 8, 4, 16, KIND_ROWST, false, 8)
 
-#define FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX) Pass<LOGL, LOGE, C, KIND, LAYOUT_IL, LAYOUT_IL, IDX>
+#define FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX) \
+    Pass<LOGL, LOGE, C, KIND, LAYOUT_IL, LAYOUT_IL, IDX, LOGX>
 
 struct BranchInfo {
-    int logl, loge, lines, kind, smem;
+    int logl, loge, lines, kind, logx, smem;
 };
-#define FFTC_BRANCH_INFO(ID, LOGL, LOGE, C, KIND, IDX) \
-    BranchInfo{LOGL, LOGE, C, KIND, FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX)::SMEM},
+#define FFTC_BRANCH_INFO(ID, LOGL, LOGE, C, KIND, IDX, LOGX) \
+    BranchInfo{LOGL, LOGE, C, KIND, LOGX, FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)::SMEM},
 static const BranchInfo kBranches[] = {FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_INFO)};
 static const int kNumBranches = sizeof(kBranches) / sizeof(kBranches[0]);
 
-#define FFTC_BRANCH_CHECK(ID, LOGL, LOGE, C, KIND, IDX) \
-    static_assert(FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX)::NT == 256, "uneven branches use 256 threads");
+#define FFTC_BRANCH_CHECK(ID, LOGL, LOGE, C, KIND, IDX, LOGX)                             \
+    static_assert(FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)::NT == 256,        \
+                  "uneven branches use 256 threads");
 FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_CHECK)
 
 static constexpr int kUnevenThreads = 256;
@@ -84,6 +94,16 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Drop the L2 lines of workspace rows a pass-2 tile has finished reading (`elems`
+// complex elements from `ws`): the workspace is never read again in this launch, so its
+// dirty lines need not be written back to HBM.
+__device__ __forceinline__ void discard_rows(const float *ws, int elems) {
+    __syncthreads();  // every load of the tile has returned
+    const char *base = reinterpret_cast<const char *>(ws);
+    for (int o = threadIdx.x * 128; o < elems * 8; o += kUnevenThreads * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + o) : "memory");
 }
 
 __global__ void __launch_bounds__(kUnevenThreads, 3) k_uneven(const __grid_constant__ PersArgs a) {
@@ -112,8 +132,11 @@ __global__ void __launch_bounds__(kUnevenThreads, 3) k_uneven(const __grid_const
         if (p.in_user) p.in = reinterpret_cast<const float *>(reinterpret_cast<const char *>(a.in) + (intptr_t)p.in);
         if (p.out_user) p.out = reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (intptr_t)p.out);
         switch (it.branch) {
-#define FFTC_BRANCH_CASE(ID, LOGL, LOGE, C, KIND, IDX) \
-    case ID: FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX)::run_tile(p, it.tile, sm_pers); break;
+#define FFTC_BRANCH_CASE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)                                       \
+    case ID:                                                                                       \
+        FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)::run_tile(p, it.tile, sm_pers);        \
+        if (KIND == KIND_ROWST) discard_rows(p.in + 2 * (int64_t)it.tile * C * (1 << LOGL), C << LOGL); \
+        break;
             FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_CASE)
             default: break;
         }
@@ -145,10 +168,10 @@ struct UnevenState {
     int64_t total_elems = 0;
 };
 
-static int find_branch(int kind, int logl, int loge, int lines) {
+static int find_branch(int kind, int logl, int loge, int lines, int logx = 0) {
     for (int i = 0; i < kNumBranches; ++i)
         if (kBranches[i].kind == kind && kBranches[i].logl == logl && kBranches[i].loge == loge &&
-            kBranches[i].lines == lines)
+            kBranches[i].lines == lines && kBranches[i].logx == logx)
             return i;
     return -1;
 }
@@ -165,13 +188,13 @@ static int env_int(const char *name, int dflt) {
 
 
 static int rows_branch(int logn) { return find_branch(KIND_ROWS, logn, 4, 256 >> (logn - 4)); }
-static int cols_branch(int logl) { return find_branch(KIND_COLS, logl, logl - 4, 16); }
-static int rowst_branch(int logl) { return find_branch(KIND_ROWST, logl, logl - 4, 16); }
+static int cols_branch(int logm, int logk) { return find_branch(KIND_COLS, logm, logm - 4, 16, logk); }
+static int rowst_branch(int logk, int logm) { return find_branch(KIND_ROWST, logk, logk - 4, 16, logm); }
 
 static bool class_supported(int logn, const ClassCfg &c) {
     if (c.logm == 0) return rows_branch(logn) >= 0;
     const int logk = logn - c.logm;
-    return cols_branch(c.logm) >= 0 && rowst_branch(logk) >= 0;
+    return cols_branch(c.logm, logk) >= 0 && rowst_branch(logk, c.logm) >= 0;
 }
 
 int uneven_max_logn(const fftc_plan_s *p) { return p->uneven ? p->uneven->max_logn : 0; }
@@ -302,8 +325,19 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
         ws = (float2 *)d;
     }
 
-    // work items: pass-1 tiles (largest first), single-pass tiles (largest first), pass-2 tiles
+    // Work items. The pass-2 tiles of a four-step transform are queued once FFTC_UNEVEN_LAG_MB
+    // (default 24) of later pass-1 input has been queued behind its pass-1 tiles: late enough
+    // that they rarely wait, early enough that the workspace is still in L2. Single-pass tiles
+    // follow, then the pass-2 tiles still pending.
     std::vector<WorkItem> p1, p0, p2;
+    struct Pending {
+        double release;
+        std::vector<WorkItem> items;
+    };
+    std::vector<Pending> pend;
+    size_t pend_head = 0;
+    double queued_bytes = 0.0;
+    const double lag_bytes = (double)env_int("FFTC_UNEVEN_LAG_MB", 24) * (1 << 20);
     int n_done = 0;
     int64_t ws_off = 0;
     for (auto it = by_log.rbegin(); it != by_log.rend(); ++it) {
@@ -343,7 +377,7 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
         } else {
             const int logm = c.logm, logk = logn - logm;
             const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
-            const int b1 = cols_branch(logm), b2 = rowst_branch(logk);
+            const int b1 = cols_branch(logm, logk), b2 = rowst_branch(logk, logm);
             float2 *tw1 = nullptr, *tw2 = nullptr;
             fftc_status s = stage_table(logm, kBranches[b1].loge, &tw1);
             if (s != FFTC_OK) return s;
@@ -403,13 +437,25 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
                 const int done = n_done++;
                 const int64_t t1 = K / 16, t2 = M / 16;
                 for (int64_t t = 0; t < t1; ++t) p1.push_back(WorkItem{b1, pa, (int32_t)t, -1, 0, done});
-                for (int64_t t = 0; t < t2; ++t) p2.push_back(WorkItem{b2, pb, (int32_t)t, done, (int32_t)t1, -1});
+                queued_bytes += 8.0 * nn;
+                Pending pd;
+                pd.release = queued_bytes + lag_bytes;
+                for (int64_t t = 0; t < t2; ++t) pd.items.push_back(WorkItem{b2, pb, (int32_t)t, done, (int32_t)t1, -1});
+                pend.push_back(pd);
+                while (pend_head < pend.size() && pend[pend_head].release <= queued_bytes) {
+                    p1.insert(p1.end(), pend[pend_head].items.begin(), pend[pend_head].items.end());
+                    ++pend_head;
+                }
                 ws_off += nn;
             }
         }
     }
-    if (env_int("FFTC_TEST_UNREACHABLE_WAIT", 0))  // test hook: a dependency nothing satisfies
+    for (; pend_head < pend.size(); ++pend_head) p2.insert(p2.end(), pend[pend_head].items.begin(), pend[pend_head].items.end());
+    if (env_int("FFTC_TEST_UNREACHABLE_WAIT", 0)) {  // test hook: a dependency nothing satisfies
+        for (WorkItem &w : p1)
+            if (w.wait_idx >= 0) w.wait_target += 1;
         for (WorkItem &w : p2) w.wait_target += 1;
+    }
     u->items = p1;
     u->items.insert(u->items.end(), p0.begin(), p0.end());
     u->items.insert(u->items.end(), p2.begin(), p2.end());
