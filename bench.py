@@ -42,6 +42,21 @@ def flops(n: int, batch: int) -> float:
     return 5.0 * n * math.log2(n) * batch
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, step_flops: float, steps: int, ms: float) -> float:
+    """Whole-job GFLOP/s: every rank runs the same sweep, time = the slowest rank."""
+    return world * step_flops * steps / (ms * 1e-3) / 1e9
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -212,10 +227,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    if dist:
-        tm = torch.tensor([ms], device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
+    ms = max_over_ranks(ms, dist, dev)
 
     # per-kernel durations from the library's event probe
     kinds = {}
@@ -246,7 +258,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / (dom_avg_ms * 1e-3) / 1e9
     step_flops = sum(flops(1 << e, ELEMS // (1 << e)) for e, *_ in plans)
-    value = world * step_flops * args.steps / (ms * 1e-3) / 1e9
+    value = weak_scaling_value(world, step_flops, args.steps, ms)
 
     # end to end: host buffers in and out through fftc_execute_host, copies timed
     e2e = None
@@ -262,10 +274,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
                 p.execute_host(h_in, h_out, y)
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
-        if dist:
-            tm = torch.tensor([wall], device=dev)
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            wall = float(tm.item())
+        wall = max_over_ranks(wall, dist, dev)
         e2e = {"value": world * step_flops * args.e2e_steps / wall / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * ELEMS * len(plans), "d2h_bytes_per_step": 8 * ELEMS * len(plans),
                "steps": args.e2e_steps}

@@ -147,6 +147,16 @@ fftc_plan fftc_plan_create_uneven(int64_t count, const int64_t *n, const int8_t 
 fftc_status fftc_plan_check(fftc_plan plan, void *stream);
 
 /*
+ * Host-only inspection of the twiddle diagonals D of Eq. 1 (Table 1 "Mul") that a pass of
+ * length L = 2^logl with radix 2^loge uses: writes the per-stage tables (stage s >= 1 holds
+ * w_{Ns R}^{t k} at [(t-1) Ns + k], t = 1..R-1, k < Ns, stages concatenated; w_L = exp(-2 pi i/L))
+ * as interleaved float pairs into `out` (host memory, room for `capacity` pairs) and returns
+ * the number of pairs through *count. Needs no GPU. FFTC_ERR_INVALID_VALUE if
+ * 1 <= loge <= logl <= 20 does not hold or the buffer is too small.
+ */
+fftc_status fftc_stage_twiddles(int logl, int loge, float *out, int64_t capacity, int64_t *count);
+
+/*
  * Timing probe for benchmarks. With enable != 0 every later execute of the plan records
  * a CUDA event on its stream before the first pass, between passes and after the last
  * pass (at most 4096 executes are kept; later ones are not recorded). With enable == 0

@@ -40,6 +40,7 @@ PROTOTYPES = {
     "fftc_plan_timing": (_c_int, [_vp, _c_int]),
     "fftc_plan_pass_times": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
     "fftc_execute_noalloc": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _vp, _vp, _vp]),
+    "fftc_stage_twiddles": (_c_int, [_c_int, _c_int, _vp, _c_i64, ctypes.POINTER(_c_i64)]),
 }
 
 _lib = None

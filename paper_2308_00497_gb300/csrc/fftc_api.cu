@@ -319,6 +319,20 @@ fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_ou
     return FFTC_OK;
 }
 
+fftc_status fftc_stage_twiddles(int logl, int loge, float *out, int64_t capacity, int64_t *count) {
+    if (loge < 1 || loge > logl || logl > 20 || !count) return FFTC_ERR_INVALID_VALUE;
+    std::vector<float2> t;
+    stage_twiddles(logl, loge, t);
+    const int64_t used = host_sched(logl, loge).tw_total;
+    *count = used;
+    if (used > capacity || (used > 0 && !out)) return FFTC_ERR_INVALID_VALUE;
+    for (int64_t i = 0; i < used; ++i) {
+        out[2 * i] = t[(size_t)i].x;
+        out[2 * i + 1] = t[(size_t)i].y;
+    }
+    return FFTC_OK;
+}
+
 fftc_status fftc_plan_timing(fftc_plan plan, int enable) {
     if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
     plan_probe_free(plan);

@@ -1,0 +1,60 @@
+"""Host logic of the multi-rank benchmark run (replicas, one per rank) on CPU with two
+gloo ranks: the reported time is the slowest rank's, the value aggregates all ranks, and
+the reference arm prints from rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+WORKER = r"""
+import os, sys, json
+sys.path.insert(0, os.environ["ROOT"])
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo")
+r = dist.get_rank()
+t = bench.max_over_ranks(10.0 + 5.0 * r, dist)
+v = bench.weak_scaling_value(dist.get_world_size(), 1e9, 4, t)
+print(json.dumps({"rank": r, "max_ms": t, "value": v}), flush=True)
+dist.barrier()
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, ROOT=ROOT, RANK=str(r), WORLD_SIZE="2", LOCAL_RANK=str(r),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", WORKER], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    import json
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for o in outs:
+        assert o["max_ms"] == 15.0
+        assert abs(o["value"] - 2 * 1e9 * 4 / 0.015 / 1e9) < 1e-6
+
+
+def test_reference_arm_prints_from_rank_zero_only(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        steps, warmup = 1, 0
+    bench.run_reference(A(), rank=1, world=2)
+    assert capsys.readouterr().out == ""
