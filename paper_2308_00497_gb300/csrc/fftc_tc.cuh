@@ -99,43 +99,83 @@ struct TcPass {
         return (g >> p.log_lpt) * tr + (g & ((int64_t(1) << p.log_lpt) - 1)) * line;
     }
 
-    __device__ static void copy_in(const PassParams &p, float2 *buf, int64_t g0) {
-        constexpr bool TAU = (KIND != KIND_COLS);
-        for (int i = threadIdx.x; i < C * L; i += NT) {
-            const int c = TAU ? i / L : i % C, a = TAU ? i % L : i / C;
-            const int64_t g = g0 + c;
-            float2 x = make_float2(0.f, 0.f);
-            if (g < p.total_lines) {
-                const int64_t off = line_base(p, g, p.in_tr, p.in_line) + (int64_t)a * p.in_elem;
-                if constexpr (LIN == LAYOUT_IL) {
-                    if constexpr (KIND == KIND_ROWST) x = __ldcg(reinterpret_cast<const float2 *>(p.in) + off);
-                    else x = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
-                } else {
-                    x.x = __ldcs(p.in + off);
-                    x.y = __ldcs(p.in + p.in_plane + off);
-                }
-                if (p.conj_in) x.y = -x.y;
-            }
-            buf[c * PITCH + rp(a)] = x;
+    // Element (c, a) of the tile handled by iteration `it` of thread `tid`. Row-contiguous
+    // kinds walk a line with consecutive threads; the column kind walks C lines.
+    static constexpr int ITER = C * L / NT;
+    static_assert(ITER * NT == C * L, "whole tiles per thread");
+    template <bool TAU>
+    __device__ __forceinline__ static void coord(int tid, int it, int &c, int &a) {
+        const int i = tid + it * NT;
+        if constexpr (TAU) {
+            c = i >> LOGL;
+            a = i & (L - 1);
+        } else {
+            c = i % C;
+            a = i / C;
         }
     }
 
+    // HBM -> shared, all loads of a thread issued before its first store
+    __device__ static void copy_in(const PassParams &p, float2 *buf, int64_t g0) {
+        constexpr bool TAU = (KIND != KIND_COLS);
+        constexpr int CH = ITER < 16 ? ITER : 16;  // loads in flight per thread
+        const int es = (int)p.in_elem;
+#pragma unroll
+        for (int b0 = 0; b0 < ITER; b0 += CH) {
+            float2 x[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                int c, a;
+                coord<TAU>(threadIdx.x, b0 + u, c, a);
+                const int64_t g = g0 + c;
+                x[u] = make_float2(0.f, 0.f);
+                if (g < p.total_lines) {
+                    const int64_t off = line_base(p, g, p.in_tr, p.in_line) + (int64_t)a * es;
+                    if constexpr (LIN == LAYOUT_IL) {
+                        if constexpr (KIND == KIND_ROWST) x[u] = __ldcg(reinterpret_cast<const float2 *>(p.in) + off);
+                        else x[u] = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
+                    } else {
+                        x[u].x = __ldcs(p.in + off);
+                        x[u].y = __ldcs(p.in + p.in_plane + off);
+                    }
+                    if (p.conj_in) x[u].y = -x[u].y;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                int c, a;
+                coord<TAU>(threadIdx.x, b0 + u, c, a);
+                buf[c * PITCH + rp(a)] = x[u];
+            }
+        }
+    }
+
+    // shared -> HBM (with the inter-pass twiddle for the column kind)
     __device__ static void copy_out(const PassParams &p, const float2 *buf, int64_t g0) {
         constexpr bool TAU = (KIND == KIND_ROWS);
-        for (int i = threadIdx.x; i < C * L; i += NT) {
-            const int c = TAU ? i / L : i % C, a = TAU ? i % L : i / C;
+        const int es = (int)p.out_elem;
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            int c, a;
+            coord<TAU>(threadIdx.x, it, c, a);
             const int64_t g = g0 + c;
             if (g >= p.total_lines) continue;
             float2 x = buf[c * PITCH + rp(a)];
-            const int64_t l = g & ((int64_t(1) << p.log_lpt) - 1);
+            const int l = (int)(g & ((int64_t(1) << p.log_lpt) - 1));
             if constexpr (KIND == KIND_COLS) {
-                const int64_t m = (l * a) & ((int64_t(1) << p.log_n2) - 1);
-                x = cmul(x, cmul(__ldg(p.tw2_lo + (m & ((int64_t(1) << p.tw2_lo_bits) - 1))),
-                                 __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
+                if (p.tw2_full) {
+                    x = cmul(x, __ldg(p.tw2_full + l * (int)p.out_line + a * es));
+                } else {
+                    const int m = (l * a) & ((1 << p.log_n2) - 1);
+                    x = cmul(x, cmul(__ldg(p.tw2_lo + (m & ((1 << p.tw2_lo_bits) - 1))),
+                                     __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
+                }
             }
             if (p.conj_out) x.y = -x.y;
-            const int64_t off = line_base(p, g, p.out_tr, p.out_line) + (int64_t)a * p.out_elem;
-            if constexpr (LOUT == LAYOUT_IL) {
+            const int64_t off = line_base(p, g, p.out_tr, p.out_line) + (int64_t)a * es;
+            if constexpr (KIND == KIND_COLS) {
+                __stcg(reinterpret_cast<float2 *>(p.out) + off, x);
+            } else if constexpr (LOUT == LAYOUT_IL) {
                 __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
             } else {
                 __stcs(p.out + off, x.x);
@@ -174,7 +214,7 @@ struct TcPass {
             const int j = j0 + g;
             float2 x[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = s[rp(j + tt[u] * ROW)];
+            for (int u = 0; u < 4; ++u) x[u] = s[j + tt[u] * (ROW + 2)];  // = rp(j + t ROW), j < ROW
             if constexpr (NS > 1) {
                 const int k = j & (NS - 1);
 #pragma unroll
