@@ -1,7 +1,7 @@
 // Planner and executor of the FP32 Stockham path.
 //
-// n <= 2^13: one fused pass (KIND_ROWS), each CTA transforming whole rows.
-// n >  2^13: Eq. 1 applied once at the HBM level, n = M * K (four-step):
+// n <= 2^14: one fused pass (KIND_ROWS), each CTA transforming whole rows.
+// n >  2^14: Eq. 1 applied once at the HBM level, n = M * K (four-step):
 //   pass 1 (KIND_COLS):  K column FFTs of length M over x[t*K + b], times w_n^(b t'),
 //                        written in place to the workspace z[t'*K + b];
 //   pass 2 (KIND_ROWST): M row FFTs of length K over z[t'*K .. t'*K + K), written
@@ -19,7 +19,7 @@
 
 namespace fftc {
 
-static const int kMaxSinglePassLog = 13;
+static const int kMaxSinglePassLog = 14;
 static const int kPassLines = 16;
 
 static int env_int(const char *name, int dflt) {

@@ -171,7 +171,7 @@ def test_l2_resident_many_groups_ring_wrap_and_tail(monkeypatch, layout, inverse
     assert rel_l2_rows(y, ref).max() <= tol_fp32(n)
 
 
-@pytest.mark.parametrize("e", [14, 15, 17, 20])
+@pytest.mark.parametrize("e", [15, 16, 17, 20])
 def test_l2_resident_matches_two_launch_path(monkeypatch, e):
     import paper_2308_00497_gb300 as fc
     n = 1 << e
@@ -190,7 +190,7 @@ def test_l2_resident_matches_two_launch_path(monkeypatch, e):
     assert err.max() <= 2 * tol_fp32(n)
 
 
-@pytest.mark.parametrize("e", [14, 17, 20])
+@pytest.mark.parametrize("e", [15, 17, 20])
 @pytest.mark.parametrize("layout", ["interleaved", "split"])
 def test_tensor_map_fed_four_step(monkeypatch, e, layout):
     """The bulk-copy / tensor-map fed four-step passes (opt-in) against the oracle."""
@@ -208,7 +208,7 @@ def test_tensor_map_fed_four_step(monkeypatch, e, layout):
     assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
 
 
-@pytest.mark.parametrize("e", [9, 10, 11, 12, 13])
+@pytest.mark.parametrize("e", [9, 10, 11, 12, 13, 14])
 @pytest.mark.parametrize("pipe", ["0", "1"])
 def test_single_pass_both_kernels(monkeypatch, e, pipe):
     """Single-pass sizes through the bulk-copy fed persistent kernel and the plain one."""
