@@ -241,7 +241,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
         if passes == 2:
             names = ["cols", "rowst"]
         else:  # one launch: a single-pass kernel, or both four-step passes in one L2-resident launch
-            names = ["rows"] if n <= (1 << 13) else ["fourstep_l2"]
+            names = ["rows"] if n <= (1 << 14) else ["fourstep_l2"]
         for i, nm in enumerate(names):
             k = kinds.setdefault(nm, {"ms": 0.0, "launches": 0})
             k["ms"] += pm[i]
