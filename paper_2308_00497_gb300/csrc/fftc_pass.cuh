@@ -40,6 +40,12 @@ __host__ __device__ constexpr int pass_pitch(int line_words, int lines) {
     return lines == 1 ? line_words : line_words + (lines >= 16 ? 1 : 2);
 }
 
+// no-op tile hook (see Pass::run_tile_landed)
+struct NoHook {
+    static constexpr bool active = false;
+    __device__ __forceinline__ void operator()() const {}
+};
+
 template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0>
 struct Pass {
     using Sc = Sched<LOGL, LOGE>;
@@ -207,8 +213,9 @@ struct Pass {
         }
     }
 
-    template <int s, bool LANDED = false>
-    __device__ __forceinline__ static void stage(const PassParams &p, float2 *sm, float2 (&v)[E], int tid, int64_t g0) {
+    template <int s, bool LANDED = false, class H = NoHook>
+    __device__ __forceinline__ static void stage(const PassParams &p, float2 *sm, float2 (&v)[E], int tid, int64_t g0,
+                                                 const H &hook = H()) {
         constexpr int LR = Sc::lr(s), R = 1 << LR, LNS = Sc::lns(s), NS = 1 << LNS;
         constexpr bool TF = tau_fast(s);
         const int c = TF ? tid / TPL : tid % C;
@@ -233,6 +240,10 @@ struct Pass {
 #pragma unroll
                     for (int t = 0; t < R; ++t) v[q * R + t] = src[t * (L / R)];
                 }
+            }
+            if constexpr (H::active && s == S - 1) {
+                __syncthreads();  // the last shared read of the tile is done: the buffer is free
+                hook();
             }
             const float2 *tw = p.tw + Sc::tw_off(s);
 #pragma unroll
@@ -261,7 +272,7 @@ struct Pass {
                 }
             }
             sync();
-            stage<s + 1, LANDED>(p, sm, v, tid, g0);
+            stage<s + 1, LANDED>(p, sm, v, tid, g0, hook);
         } else {
             store_global<R>(p, v, tau, g, live);
         }
@@ -279,10 +290,13 @@ struct Pass {
         stage<0>(p, sm, v, threadIdx.x, tile * C);
     }
 
-    // one tile whose input lines already sit in `sm` (line c at c * PITCH)
-    __device__ __forceinline__ static void run_tile_landed(const PassParams &p, int64_t tile, float2 *sm) {
+    // one tile whose input lines already sit in `sm` (see landed()); `hook` runs once,
+    // by every thread, as soon as the tile's last shared-memory read is done
+    template <class H = NoHook>
+    __device__ __forceinline__ static void run_tile_landed(const PassParams &p, int64_t tile, float2 *sm,
+                                                           const H &hook = H()) {
         float2 v[E];
-        stage<0, true>(p, sm, v, threadIdx.x, tile * C);
+        stage<0, true>(p, sm, v, threadIdx.x, tile * C, hook);
     }
 };
 

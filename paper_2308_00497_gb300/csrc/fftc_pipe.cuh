@@ -13,6 +13,13 @@
 // tile with stage 0 reading the landed data and the exchanges reusing the same buffer,
 // writes the result to HBM from registers, and only then refills the buffer with tile
 // k + NBUF. So NBUF - 1 tiles of HBM reads are in flight behind the compute.
+//
+// EARLY variant: the refill is issued as soon as the tile's last shared-memory read is
+// done, before its last radix stage and its HBM stores, so even NBUF = 1 keeps one tile's
+// reads in flight behind the end of the previous tile; this lets a 135 KB tile (one CTA
+// per SM) or two 68 KB tiles per SM overlap their loads with compute.
+// (A per-thread 16-byte cp.async feed of the narrow pass-1 column bands measured slower
+// than plain loads into registers, and tensor-map boxes of 64-byte rows slower still.)
 #pragma once
 
 #include <cuda.h>
@@ -88,7 +95,7 @@ struct PipeArgs {
     CUtensorMap tm[2];  // four-step pass 1: input (real plane / interleaved) and imaginary plane
 };
 
-template <class P, int NBUF>
+template <class P, int NBUF, bool EARLY = false>
 struct PipeTile {
     static_assert(P::S > 1, "pipelined tiles need an exchange buffer");
     static constexpr int KIND = P::KIND_ID;
@@ -142,6 +149,26 @@ struct PipeTile {
         }
     }
 
+    // refill `buf` with `tile`: called by every thread after a block-wide barrier that
+    // ends the buffer's shared reads
+    __device__ __forceinline__ static void refill(const PipeArgs &a, int64_t tile, float2 *buf, uint64_t *bar) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            issue(a, tile, buf, bar);
+        }
+    }
+
+    struct Refill {
+        static constexpr bool active = true;
+        const PipeArgs *a;
+        int64_t tile;
+        float2 *buf;
+        uint64_t *bar;
+        __device__ __forceinline__ void operator()() const {
+            if (tile >= 0) refill(*a, tile, buf, bar);
+        }
+    };
+
     __device__ static void run(const PipeArgs &a) {
         const PassParams &p = a.p;
         extern __shared__ __align__(128) unsigned char pipe_raw[];
@@ -174,46 +201,48 @@ struct PipeTile {
                 }
                 return;
             }
-            P::run_tile_landed(p, tile, bufs + b * BUF_WORDS);
-            __syncthreads();  // every shared read of buffer b is done
             const int64_t next = tile + (int64_t)NBUF * gridDim.x;
-            if (threadIdx.x == 0 && next < ntiles) {
-                fence_proxy_async_smem();
-                issue(a, next, bufs + b * BUF_WORDS, &bars[b]);
+            float2 *buf = bufs + b * BUF_WORDS;
+            if constexpr (EARLY) {
+                P::run_tile_landed(p, tile, buf, Refill{&a, next < ntiles ? next : -1, buf, &bars[b]});
+            } else {
+                P::run_tile_landed(p, tile, buf);
+                __syncthreads();  // every shared read of buffer b is done
+                if (next < ntiles) refill(a, next, buf, &bars[b]);
             }
         }
     }
 };
 
-template <class P, int NBUF>
+template <class P, int NBUF, bool EARLY>
 __global__ void __launch_bounds__(P::NT, P::MINB) k_pipe(const __grid_constant__ PipeArgs a) {
-    PipeTile<P, NBUF>::run(a);
+    PipeTile<P, NBUF, EARLY>::run(a);
 }
 
 // host: encode the tensor map(s) of a four-step pass-1 input (see PipeTile::issue)
 bool encode_cols_maps(const PassParams &p, int logl, int lines, int lay, CUtensorMap *tm);
 
-template <class P, int NBUF>
+template <class P, int NBUF, bool EARLY>
 struct PipeLauncher {
+    using PT = PipeTile<P, NBUF, EARLY>;
     static int &grid_cache() {
         static int g = 0;
         return g;
     }
     static cudaError_t prepare() {
-        using PT = PipeTile<P, NBUF>;
-        cudaError_t e = cudaFuncSetAttribute(k_pipe<P, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_pipe<P, NBUF, EARLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0, dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipe<P, NBUF>, PT::NT, PT::SMEM)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipe<P, NBUF, EARLY>, PT::NT,
+                                                               PT::SMEM)) != cudaSuccess)
             return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid_cache() = (per_sm > 0 ? per_sm : 1) * sms;
         return cudaSuccess;
     }
     static cudaError_t launch(const PassParams &p, cudaStream_t st) {
-        using PT = PipeTile<P, NBUF>;
         const int64_t ntiles = (p.total_lines + PT::C - 1) / PT::C;
         if (ntiles <= 0) return cudaSuccess;
         if (grid_cache() == 0) {
@@ -227,18 +256,21 @@ struct PipeLauncher {
             if (!encode_cols_maps(p, P::L == 0 ? 0 : __builtin_ctz(P::L), PT::C, P::LIN_LAYOUT, a.tm))
                 return cudaErrorInvalidValue;
         const int grid = (int)(ntiles < grid_cache() ? ntiles : grid_cache());
-        k_pipe<P, NBUF><<<grid, PT::NT, PT::SMEM, st>>>(a);
+        k_pipe<P, NBUF, EARLY><<<grid, PT::NT, PT::SMEM, st>>>(a);
         return cudaGetLastError();
     }
 };
 
-// registry entry of a pipelined pass kernel (`pipe` = NBUF)
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int NBUF>
+// `pipe` code of a registry entry: NBUF | 4 * EARLY
+constexpr int pipe_code(int nbuf, bool early) { return nbuf | (early ? 4 : 0); }
+
+// registry entry of a pipelined pass kernel
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int NBUF, bool EARLY = false>
 constexpr KernelEntry pipe_entry() {
     using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
-    using L = PipeLauncher<P, NBUF>;
-    return KernelEntry{KIND, LOGL, LOGE, C, LIN, LOUT, P::NT, PipeTile<P, NBUF>::SMEM, &L::launch, &L::prepare, 0,
-                       LOGX, NBUF};
+    using L = PipeLauncher<P, NBUF, EARLY>;
+    return KernelEntry{KIND,          LOGL, LOGE, C, LIN, LOUT, P::NT, PipeTile<P, NBUF, EARLY>::SMEM,
+                       &L::launch,    &L::prepare, 0, LOGX, pipe_code(NBUF, EARLY)};
 }
 
 }  // namespace fftc

@@ -52,15 +52,35 @@ bool choose_four_step(int logn, int *logm, int *loge1, int *loge2, int *lines1, 
     int m = env_int("FFTC_TUNE_FOURSTEP_LOGM", logn / 2);
     int k = logn - m;
     *logm = m;
-    *loge1 = env_int("FFTC_TUNE_COLS_E", m >= 9 ? 5 : 4);
+    // pass 1: 16-element threads and 16-column (128-byte) bands up to M = 2^9, 32-element
+    // threads and 8-column bands at M = 2^10 (a 16-column band would need 128 KB tiles)
+    *loge1 = env_int("FFTC_TUNE_COLS_E", m >= 10 ? 5 : 4);
     *loge2 = env_int("FFTC_TUNE_ROWST_E", k >= 9 ? 5 : 4);
     if (*loge1 > m) *loge1 = m;
     if (*loge2 >= k) *loge2 = k - 1;
-    // 8-line tiles (two CTAs per SM) where the line is long, 16-line tiles otherwise
-    if (lines1) *lines1 = env_int("FFTC_TUNE_COLS_C", m >= 9 ? 8 : 16);
+    // pass 2: 8-line tiles (two CTAs per SM) where the line is long, 16-line tiles otherwise
+    if (lines1) *lines1 = env_int("FFTC_TUNE_COLS_C", m >= 10 ? 8 : 16);
     if (lines2) *lines2 = env_int("FFTC_TUNE_ROWST_C", k >= 9 ? 8 : 16);
     return true;
 }
+
+// Default pipelined single-pass kernel per size: elements per thread (log2), lines per
+// tile, pipe code (landing buffers | 4 when the refill follows the last shared read).
+struct PipeRowsDefault {
+    int logn, loge, lines, code;
+};
+static const PipeRowsDefault kPipeRowsDefaults[] = {
+    {9, 5, 8, 2}, {10, 5, 4, 2}, {11, 5, 2, 6}, {12, 4, 1, 5}, {13, 5, 1, 5}, {14, 5, 1, 5},
+};
+static const PipeRowsDefault *pipe_rows_default(int logn) {
+    for (const PipeRowsDefault &d : kPipeRowsDefaults)
+        if (d.logn == logn) return &d;
+    return nullptr;
+}
+
+// Four-step pass 2 is fed by one bulk copy per tile, refilled after the last shared read,
+// from n = 2^17 (below, the plain kernel measured faster)
+static int pass2_pipe_default(int logn) { return logn >= 17 ? 6 : 0; }
 
 static fftc_status upload_stage_tables(fftc_plan_s *p, PassPlan &pp) {
     std::vector<float2> tw;
@@ -104,15 +124,18 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         }
         pp.lin = pp.lout = lay;
         pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay, prec);
-        // pipelined persistent kernel where it measured faster (n = 2^9 .. 2^11, 2^13)
-        const bool pipe_dflt = p->logn == 9 || p->logn == 10 || p->logn == 11 || p->logn == 13;
-        if (!tc && env_int("FFTC_PIPE", pipe_dflt ? 1 : 0)) {
-            const int pe = env_int("FFTC_TUNE_PIPE_E", 0), pc = env_int("FFTC_TUNE_PIPE_C", 0);
-            const KernelEntry *k = find_pipe_rows(pp.logl, lay);
-            for (int i = 0; pe && i < kernel_count(); ++i) {
+        // pipelined persistent kernel where it measured faster (n = 2^9 .. 2^14)
+        const PipeRowsDefault *pd = pipe_rows_default(p->logn);
+        if (!tc && env_int("FFTC_PIPE", pd ? 1 : 0)) {
+            const int pe = env_int("FFTC_TUNE_PIPE_E", 0), pc = env_int("FFTC_TUNE_PIPE_C", 0),
+                      pk = env_int("FFTC_TUNE_PIPE_CODE", 0);
+            const KernelEntry *k =
+                pd ? find_kernel(KIND_ROWS, pp.logl, pd->loge, pd->lines, lay, lay, 0, 0, pd->code) : nullptr;
+            if (!k) k = find_pipe_rows(pp.logl, lay);
+            for (int i = 0; (pe || pc || pk) && i < kernel_count(); ++i) {
                 const KernelEntry *e = kernel_at(i);
-                if (e->pipe && e->kind == KIND_ROWS && e->logl == pp.logl && e->lin == lay && e->loge == pe &&
-                    (!pc || e->lines == pc))
+                if (e->pipe && e->kind == KIND_ROWS && e->logl == pp.logl && e->lin == lay && (!pe || e->loge == pe) &&
+                    (!pc || e->lines == pc) && (!pk || e->pipe == pk))
                     k = e;
             }
             if (k) {
@@ -195,9 +218,10 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lout = LAYOUT_IL;
         pp.k = nullptr;
         // pipelined (tensor-map fed) pass: off by default, the narrow column boxes make the
-        // bulk-copy engine issue one small request per row (FFTC_PIPE4=1 enables it)
-        if (!tc && env_int("FFTC_PIPE4", 0))
-            pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk, 2);
+        // bulk-copy engine issue one small request per row (bit 0 of FFTC_PIPE4 enables it)
+        if (!tc && (env_int("FFTC_PIPE4", 0) & 1))
+            pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk,
+                               env_int("FFTC_TUNE_P1_PIPE", 2));
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
@@ -231,8 +255,11 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
         pp.k = nullptr;
-        if (!tc && env_int("FFTC_PIPE4", 0))
-            pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm, 2);
+        // bit 1 of FFTC_PIPE4: bulk-copy fed pass 2
+        const int p2 = pass2_pipe_default(p->logn);
+        if (!tc && (env_int("FFTC_PIPE4", p2 ? 2 : 0) & 2))
+            pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm,
+                               env_int("FFTC_TUNE_P2_PIPE", p2 ? p2 : 2));
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;

@@ -4,9 +4,9 @@
 namespace fftc {
 
 extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
-    kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[];
+    kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[];
 extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count,
-    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count;
+    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount;
 
 struct TableRef {
     const KernelEntry *t;
@@ -17,6 +17,7 @@ static const TableRef kTables[] = {
     {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
     {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
     {kPipeRowsIlTable, &kPipeRowsIlCount}, {kPipeRowsSplitTable, &kPipeRowsSplitCount}, {kPipe4Table, &kPipe4Count},
+    {kPipeEarlyIlTable, &kPipeEarlyIlCount}, {kPipeEarlySplitTable, &kPipeEarlySplitCount},
 };
 
 int kernel_count() {

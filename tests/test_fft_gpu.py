@@ -190,12 +190,15 @@ def test_l2_resident_matches_two_launch_path(monkeypatch, e):
     assert err.max() <= 2 * tol_fp32(n)
 
 
-@pytest.mark.parametrize("e", [15, 17, 20])
+@pytest.mark.parametrize("e", [15, 16, 17, 18, 19, 20])
 @pytest.mark.parametrize("layout", ["interleaved", "split"])
-def test_tensor_map_fed_four_step(monkeypatch, e, layout):
-    """The bulk-copy / tensor-map fed four-step passes (opt-in) against the oracle."""
+@pytest.mark.parametrize("p2code", ["2", "6"])
+def test_tensor_map_fed_four_step(monkeypatch, e, layout, p2code):
+    """The bulk-copy / tensor-map fed four-step passes against the oracle: pass 1 through
+    2D tensor boxes (opt-in), pass 2 refilled after its stores (2) or its last shared read (6)."""
     import paper_2308_00497_gb300 as fc
-    monkeypatch.setenv("FFTC_PIPE4", "1")
+    monkeypatch.setenv("FFTC_PIPE4", "3")
+    monkeypatch.setenv("FFTC_TUNE_P2_PIPE", p2code)
     n = 1 << e
     B = max(2, (1 << 21) // n)
     x = si.uniform_complex(B, n, seed=e + 5)
@@ -208,12 +211,14 @@ def test_tensor_map_fed_four_step(monkeypatch, e, layout):
     assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
 
 
-@pytest.mark.parametrize("e", [9, 10, 11, 12, 13, 14])
-@pytest.mark.parametrize("pipe", ["0", "1"])
-def test_single_pass_both_kernels(monkeypatch, e, pipe):
-    """Single-pass sizes through the bulk-copy fed persistent kernel and the plain one."""
+@pytest.mark.parametrize("e", [8, 9, 10, 11, 12, 13, 14])
+@pytest.mark.parametrize("pipe,code", [("0", ""), ("1", ""), ("1", "2"), ("1", "6")])
+def test_single_pass_both_kernels(monkeypatch, e, pipe, code):
+    """Single-pass sizes through the plain kernel and the bulk-copy fed persistent kernels
+    (refill after the tile's HBM stores, code 2, or after its last shared read, codes 5/6)."""
     import paper_2308_00497_gb300 as fc
     monkeypatch.setenv("FFTC_PIPE", pipe)
+    monkeypatch.setenv("FFTC_TUNE_PIPE_CODE", code)
     n = 1 << e
     B = 1000 + e  # not a multiple of any tile: the last tile is partial
     x = si.uniform_complex(B, n, seed=e)
