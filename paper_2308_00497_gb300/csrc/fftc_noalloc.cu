@@ -52,8 +52,11 @@ fftc_status setup_device(int dev, DeviceSetup &d) {
     std::vector<float2> host((size_t)kNumLogs * kTabPerLog, make_float2(0.f, 0.f));
     for (int logn = kMinLog; logn <= kMaxLog; ++logn) {
         SizeSetup &s = d.size[logn - kMinLog];
-        int c1 = 16, c2 = 16;
-        if (!choose_four_step(logn, &s.logm, &s.e1, &s.e2, &c1, &c2)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        const FourStepChoice fc = choose_four_step(logn, LAYOUT_IL);  // plain kernels of the same shapes
+        s.logm = fc.logm;
+        s.e1 = fc.e1;
+        s.e2 = fc.e2;
+        const int c1 = fc.c1, c2 = fc.c2;
         const int logk = logn - s.logm;
         for (int lay = 0; lay < 2; ++lay) {
             s.k1[lay] = find_kernel(KIND_COLS, s.logm, s.e1, c1, lay, LAYOUT_IL, 0, logk);

@@ -48,20 +48,45 @@ bool choose_rows(int logn, int lin, int *loge, int *lines) {
     return find_kernel(KIND_ROWS, logn, e, c, lin, lin) != nullptr;
 }
 
-bool choose_four_step(int logn, int *logm, int *loge1, int *loge2, int *lines1, int *lines2) {
-    int m = env_int("FFTC_TUNE_FOURSTEP_LOGM", logn / 2);
-    int k = logn - m;
-    *logm = m;
-    // pass 1: 16-element threads and 16-column (128-byte) bands up to M = 2^9, 32-element
-    // threads and 8-column bands at M = 2^10 (a 16-column band would need 128 KB tiles)
-    *loge1 = env_int("FFTC_TUNE_COLS_E", m >= 10 ? 5 : 4);
-    *loge2 = env_int("FFTC_TUNE_ROWST_E", k >= 9 ? 5 : 4);
-    if (*loge1 > m) *loge1 = m;
-    if (*loge2 >= k) *loge2 = k - 1;
-    // pass 2: 8-line tiles (two CTAs per SM) where the line is long, 16-line tiles otherwise
-    if (lines1) *lines1 = env_int("FFTC_TUNE_COLS_C", m >= 10 ? 8 : 16);
-    if (lines2) *lines2 = env_int("FFTC_TUNE_ROWST_C", k >= 9 ? 8 : 16);
-    return true;
+// Measured four-step shapes, n = M K (Eq. 1 at the memory level). Pass 1 reads bands of
+// C1 adjacent columns (C1 * 8 bytes per row, the wider the better up to the tile budget of
+// ~68 KB); pass 2 writes C2-element runs (narrower than 8 elements is slow, above all for
+// the split layout). Pass-1 feed per layout: 0 = plain loads into registers, 5 = tensor-map
+// boxes into one landing buffer refilled after the tile's last shared read; pass 2: 0 =
+// plain, 6 = one bulk copy per tile into two landing buffers, early refill.
+struct FourStepDefault {
+    int logn, logm, e1, c1, p1_il, p1_split, e2, c2, p2;
+};
+static const FourStepDefault kFourStepDefaults[] = {
+    {14, 7, 4, 16, 0, 0, 4, 16, 0},  {15, 7, 4, 16, 0, 5, 4, 16, 0}, {16, 8, 4, 16, 0, 5, 4, 16, 0},
+    {17, 8, 4, 16, 0, 5, 5, 8, 6},   {18, 8, 4, 32, 5, 5, 5, 8, 6},  {19, 9, 4, 16, 0, 5, 5, 8, 6},
+    {20, 10, 5, 8, 0, 0, 5, 8, 6},
+};
+
+FourStepChoice choose_four_step(int logn, int lay) {
+    FourStepChoice c;
+    const FourStepDefault *d = nullptr;
+    for (const FourStepDefault &t : kFourStepDefaults)
+        if (t.logn == logn) d = &t;
+    const int m = env_int("FFTC_TUNE_FOURSTEP_LOGM", d ? d->logm : logn / 2), k = logn - m;
+    const bool same = d && m == d->logm;  // the table row applies to this split
+    c.logm = m;
+    c.e1 = env_int("FFTC_TUNE_COLS_E", same ? d->e1 : (m >= 10 ? 5 : 4));
+    c.e2 = env_int("FFTC_TUNE_ROWST_E", same ? d->e2 : (k >= 9 ? 5 : 4));
+    if (c.e1 > m) c.e1 = m;
+    if (c.e2 >= k) c.e2 = k - 1;
+    c.c1 = env_int("FFTC_TUNE_COLS_C", same ? d->c1 : (m >= 10 ? 8 : 16));
+    c.c2 = env_int("FFTC_TUNE_ROWST_C", same ? d->c2 : (k >= 9 ? 8 : 16));
+    c.p1 = same ? (lay == LAYOUT_SPLIT ? d->p1_split : d->p1_il) : 0;
+    c.p2 = same ? d->p2 : 0;
+    // FFTC_PIPE4: bit 0 forces the pass-1 feed on or off (code FFTC_TUNE_P1_PIPE, default
+    // tensor-map boxes with two buffers), bit 1 the pass-2 feed (FFTC_TUNE_P2_PIPE)
+    const int force = env_int("FFTC_PIPE4", -1);
+    if (force >= 0) {
+        c.p1 = (force & 1) ? env_int("FFTC_TUNE_P1_PIPE", c.p1 ? c.p1 : 2) : 0;
+        c.p2 = (force & 2) ? env_int("FFTC_TUNE_P2_PIPE", c.p2 ? c.p2 : 2) : 0;
+    }
+    return c;
 }
 
 // Default pipelined single-pass kernel per size: elements per thread (log2), lines per
@@ -77,10 +102,6 @@ static const PipeRowsDefault *pipe_rows_default(int logn) {
         if (d.logn == logn) return &d;
     return nullptr;
 }
-
-// Four-step pass 2 is fed by one bulk copy per tile, refilled after the last shared read,
-// from n = 2^17 (below, the plain kernel measured faster)
-static int pass2_pipe_default(int logn) { return logn >= 17 ? 6 : 0; }
 
 static fftc_status upload_stage_tables(fftc_plan_s *p, PassPlan &pp) {
     std::vector<float2> tw;
@@ -161,12 +182,19 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     }
 
     // four-step: n = M * K
-    int logm, e1, e2, c1 = kPassLines, c2 = kPassLines;
+    int logm, e1, e2, c1 = kPassLines, c2 = kPassLines, p1code = 0, p2code = 0;
     if (tc) {
         logm = p->logn / 2;
         e1 = e2 = 4;
-    } else if (!choose_four_step(p->logn, &logm, &e1, &e2, &c1, &c2)) {
-        return FFTC_ERR_UNSUPPORTED_SIZE;
+    } else {
+        const FourStepChoice fc = choose_four_step(p->logn, lay);
+        logm = fc.logm;
+        e1 = fc.e1;
+        e2 = fc.e2;
+        c1 = fc.c1;
+        c2 = fc.c2;
+        p1code = fc.p1;
+        p2code = fc.p2;
     }
     const int logk = p->logn - logm;
     const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
@@ -217,11 +245,9 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lin = lay;
         pp.lout = LAYOUT_IL;
         pp.k = nullptr;
-        // pipelined (tensor-map fed) pass: off by default, the narrow column boxes make the
-        // bulk-copy engine issue one small request per row (bit 0 of FFTC_PIPE4 enables it)
-        if (!tc && (env_int("FFTC_PIPE4", 0) & 1))
-            pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk,
-                               env_int("FFTC_TUNE_P1_PIPE", 2));
+        // tensor-map fed pass where it measured faster (narrow column boxes make the
+        // bulk-copy engine issue one small request per row, so plain loads often win)
+        if (p1code) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk, p1code);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
@@ -255,11 +281,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lin = LAYOUT_IL;
         pp.lout = lay;
         pp.k = nullptr;
-        // bit 1 of FFTC_PIPE4: bulk-copy fed pass 2
-        const int p2 = pass2_pipe_default(p->logn);
-        if (!tc && (env_int("FFTC_PIPE4", p2 ? 2 : 0) & 2))
-            pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm,
-                               env_int("FFTC_TUNE_P2_PIPE", p2 ? p2 : 2));
+        if (p2code) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm, p2code);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;

@@ -84,6 +84,10 @@ void fs_free(fftc_plan_s *p);
 // Kernel choice for a pass; overridable through FFTC_TUNE_* environment variables
 // by the tuner. Returns false if no compiled kernel fits.
 bool choose_rows(int logn, int lin, int *loge, int *lines);
-bool choose_four_step(int logn, int *logm, int *loge1, int *loge2, int *lines1 = nullptr, int *lines2 = nullptr);
+struct FourStepChoice {
+    int logm, e1, c1, e2, c2;
+    int p1, p2;  // pipe codes of the two passes (0: plain kernel)
+};
+FourStepChoice choose_four_step(int logn, int lay);
 
 }  // namespace fftc

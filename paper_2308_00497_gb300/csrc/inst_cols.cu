@@ -9,9 +9,9 @@ namespace fftc {
                                 entry<LOGL, LOGE, C, KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL, LOGX>()
 
 extern const KernelEntry kColsTable[] = {
-    // n = 2^14 .. 2^20 (M x K = 7x7, 7x8, 8x8, 8x9, 9x9, 9x10, 10x10)
-    C2(7, 4, 16, 7), C2(7, 4, 16, 8), C2(8, 4, 16, 8), C2(8, 4, 16, 9), C2(9, 5, 8, 9), C2(9, 5, 8, 10),
-    C2(10, 5, 8, 10), C2(9, 4, 16, 9), C2(9, 4, 16, 10),
+    // n = 2^14 .. 2^20 (M x K = 7x7, 7x8, 8x8, 8x9, 8x10, 9x10, 10x10), and 9x9
+    C2(7, 4, 16, 7), C2(7, 4, 16, 8), C2(8, 4, 16, 8), C2(8, 4, 16, 9), C2(8, 4, 32, 10), C2(9, 4, 16, 10),
+    C2(10, 5, 8, 10), C2(9, 4, 16, 9),
     // runtime strides (tuning alternatives)
     C2(6, 4, 16, 0), C2(7, 4, 16, 0), C2(8, 4, 16, 0), C2(9, 4, 16, 0), C2(9, 5, 16, 0), C2(10, 4, 16, 0),
     C2(10, 5, 16, 0), C2(9, 5, 8, 0), C2(10, 5, 8, 0), C2(10, 4, 8, 0),

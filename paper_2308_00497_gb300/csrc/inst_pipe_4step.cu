@@ -15,10 +15,9 @@ namespace fftc {
         pipe_entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT, LOGX, NBUF>()
 
 extern const KernelEntry kPipe4Table[] = {
-    PC2(7, 4, 16, 7, 2), PC2(7, 4, 16, 8, 2), PC2(8, 4, 16, 8, 2), PC2(8, 4, 16, 9, 2), PC2(9, 5, 8, 9, 2),
-    PC2(9, 5, 8, 10, 2), PC2(10, 5, 8, 10, 2),
-    PT2(7, 4, 16, 7, 2), PT2(8, 4, 16, 7, 2), PT2(8, 4, 16, 8, 2), PT2(9, 5, 8, 8, 2), PT2(9, 5, 8, 9, 2),
-    PT2(10, 5, 8, 9, 2), PT2(10, 5, 8, 10, 2),
+    PC2(7, 4, 16, 7, 2), PC2(7, 4, 16, 8, 2), PC2(8, 4, 16, 8, 2), PC2(8, 4, 16, 9, 2), PC2(10, 5, 8, 10, 2),
+    PT2(7, 4, 16, 7, 2), PT2(8, 4, 16, 7, 2), PT2(8, 4, 16, 8, 2), PT2(9, 5, 8, 8, 2), PT2(10, 5, 8, 9, 2),
+    PT2(10, 5, 8, 10, 2),
 };
 extern const int kPipe4Count = sizeof(kPipe4Table) / sizeof(kPipe4Table[0]);
 

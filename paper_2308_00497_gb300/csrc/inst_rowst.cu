@@ -10,9 +10,9 @@ namespace fftc {
                                 entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT, LOGX>()
 
 extern const KernelEntry kRowsTTable[] = {
-    // n = 2^14 .. 2^20 (K x M = 7x7, 8x7, 8x8, 9x8, 9x9, 10x9, 10x10)
-    T2(7, 4, 16, 7), T2(8, 4, 16, 7), T2(8, 4, 16, 8), T2(9, 5, 8, 8), T2(9, 5, 8, 9), T2(10, 5, 8, 9),
-    T2(10, 5, 8, 10),
+    // n = 2^14 .. 2^20 (K x M = 7x7, 8x7, 8x8, 9x8, 10x8, 10x9, 10x10), and 9x9
+    T2(7, 4, 16, 7), T2(8, 4, 16, 7), T2(8, 4, 16, 8), T2(9, 5, 8, 8), T2(10, 5, 8, 8), T2(10, 5, 8, 9),
+    T2(10, 5, 8, 10), T2(9, 5, 8, 9),
     // runtime strides (tuning alternatives)
     T2(7, 4, 16, 0), T2(8, 4, 16, 0), T2(9, 4, 16, 0), T2(9, 5, 16, 0), T2(10, 4, 16, 0), T2(10, 5, 16, 0),
     T2(9, 5, 8, 0), T2(10, 5, 8, 0), T2(10, 4, 8, 0),
