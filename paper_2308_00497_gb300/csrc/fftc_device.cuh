@@ -18,6 +18,10 @@ __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
+// ask L2 to fetch the line holding `p` (no register result, no fault semantics needed:
+// callers pass addresses inside their buffers)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // cos(2*pi*m/64) for m = 0..16 (a quarter period): cos(pi*m/32).
 __host__ __device__ __forceinline__ float cos64_q(int m) {
     switch (m) {

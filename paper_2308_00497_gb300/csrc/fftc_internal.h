@@ -46,6 +46,11 @@ struct PassParams {
     // persistent launches: when set, `in` / `out` hold byte offsets into the launch's
     // user input / output buffers instead of pointers
     int32_t in_user, out_user;
+    // plain four-step pass 1: each CTA first asks L2 to prefetch the input band of tile
+    // blockIdx + pf_tiles (the tile a CTA launched about one tile-time later will read),
+    // so that HBM streams while this CTA computes (0 = off; < 0: the launch sets it to
+    // the number of CTAs resident at once)
+    int32_t pf_tiles;
     int *err;  // device error word of the plan (bounded waits that gave up)
 };
 

@@ -27,7 +27,7 @@ static __device__ __align__(256) float2 g_noalloc_scratch[kScratchElems];
 static __device__ __align__(256) float2 g_noalloc_tables[kNumLogs * kTabPerLog];
 
 struct SizeSetup {
-    int logm, e1, e2, lo_bits;
+    int logm, e1, e2, lo_bits, pf;
     const KernelEntry *k1[2], *k2[2];  // per layout: pass 1 (COLS), pass 2 (ROWST)
     int off_tw1, off_tw2, off_lo, off_hi;  // table offsets (float2 entries) inside this size's block
 };
@@ -56,6 +56,7 @@ fftc_status setup_device(int dev, DeviceSetup &d) {
         s.logm = fc.logm;
         s.e1 = fc.e1;
         s.e2 = fc.e2;
+        s.pf = fc.pf;
         const int c1 = fc.c1, c2 = fc.c2;
         const int logk = logn - s.logm;
         for (int lay = 0; lay < 2; ++lay) {
@@ -152,6 +153,7 @@ extern "C" fftc_status fftc_execute_noalloc(int64_t n, int64_t batch, fftc_layou
     a.log_n2 = logn;
     a.tw2_lo_bits = s.lo_bits;
     a.conj_in = inv;
+    a.pf_tiles = s.pf ? -1 : 0;
     if (s.k1[lay]->launch(a, st) != cudaSuccess) return FFTC_ERR_CUDA;
 
     PassParams b{};

@@ -278,8 +278,32 @@ struct Pass {
         }
     }
 
+    // ask L2 to fetch the input rows of `tile` (pass 1: L rows of C adjacent columns),
+    // one prefetch per 32-byte sector
+    __device__ __forceinline__ static void prefetch_tile(const PassParams &p, int64_t tile) {
+        const int64_t g0 = tile * C;
+        if (g0 >= p.total_lines) return;
+        const int64_t base = line_off(p, g0, p.in_tr, p.in_line);
+        const int64_t es = ES_IN_CT ? ES_IN_CT : p.in_elem;
+        if constexpr (LIN == LAYOUT_IL) {
+            constexpr int SPR = (C * 8 + 31) / 32;  // sectors per row
+            const char *b = reinterpret_cast<const char *>(p.in + 2 * base);
+            for (int i = threadIdx.x; i < L * SPR; i += NT)
+                prefetch_l2(b + (i / SPR) * es * 8 + (i % SPR) * 32);
+        } else {
+            constexpr int SPR = (C * 4 + 31) / 32;
+            for (int i = threadIdx.x; i < 2 * L * SPR; i += NT) {
+                const int h = i / (L * SPR), j = i % (L * SPR);
+                prefetch_l2(reinterpret_cast<const char *>(p.in + h * p.in_plane + base + (j / SPR) * es) +
+                            (j % SPR) * 32);
+            }
+        }
+    }
+
     __device__ __forceinline__ static void run(const PassParams &p) {
         extern __shared__ float2 sm_dyn[];
+        if constexpr (KIND == KIND_COLS && !IDX)
+            if (p.pf_tiles > 0) prefetch_tile(p, (int64_t)blockIdx.x + p.pf_tiles);
         float2 v[E];
         stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
     }
@@ -307,12 +331,37 @@ __global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LO
     Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::run(p);
 }
 
+// CTAs of a k_pass instance resident on the current device at once (0 if unknown)
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
+int resident_ctas() {
+    static int r = -1;
+    if (r < 0) {
+        using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
+        int per_sm = 0, sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>, P::NT,
+                                                          P::SMEM) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        r = per_sm * sms;
+    }
+    return r;
+}
+
 template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
 cudaError_t launch_pass(const PassParams &p, cudaStream_t st) {
     using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
     const int64_t blocks = (p.total_lines + C - 1) / C;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    if constexpr (KIND == KIND_COLS) {
+        if (p.pf_tiles < 0) {
+            PassParams q = p;
+            q.pf_tiles = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>();
+            k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(q);
+            return cudaGetLastError();
+        }
+    }
     k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
     return cudaGetLastError();
 }

@@ -54,13 +54,15 @@ bool choose_rows(int logn, int lin, int *loge, int *lines) {
 // the split layout). Pass-1 feed per layout: 0 = plain loads into registers, 5 = tensor-map
 // boxes into one landing buffer refilled after the tile's last shared read; pass 2: 0 =
 // plain, 6 = one bulk copy per tile into two landing buffers, early refill.
+// A plain pass 1 also prefetches, into L2, the band of the tile launched one wave later
+// (pf = 1) where that measured faster.
 struct FourStepDefault {
-    int logn, logm, e1, c1, p1_il, p1_split, e2, c2, p2;
+    int logn, logm, e1, c1, p1_il, p1_split, pf, e2, c2, p2;
 };
 static const FourStepDefault kFourStepDefaults[] = {
-    {14, 7, 4, 16, 0, 0, 4, 16, 0},  {15, 7, 4, 16, 0, 5, 4, 16, 0}, {16, 8, 4, 16, 0, 5, 4, 16, 0},
-    {17, 8, 4, 16, 0, 5, 5, 8, 6},   {18, 8, 4, 32, 5, 5, 5, 8, 6},  {19, 9, 4, 16, 0, 5, 5, 8, 6},
-    {20, 10, 5, 8, 0, 0, 5, 8, 6},
+    {14, 7, 4, 16, 0, 0, 1, 4, 16, 0}, {15, 7, 4, 16, 0, 5, 1, 4, 16, 0}, {16, 8, 4, 16, 0, 5, 1, 4, 16, 0},
+    {17, 8, 4, 16, 0, 5, 1, 5, 8, 6},  {18, 8, 4, 32, 5, 5, 1, 5, 8, 6},  {19, 9, 4, 16, 0, 5, 1, 5, 8, 6},
+    {20, 10, 5, 8, 0, 0, 0, 5, 8, 6},
 };
 
 FourStepChoice choose_four_step(int logn, int lay) {
@@ -79,6 +81,7 @@ FourStepChoice choose_four_step(int logn, int lay) {
     c.c2 = env_int("FFTC_TUNE_ROWST_C", same ? d->c2 : (k >= 9 ? 8 : 16));
     c.p1 = same ? (lay == LAYOUT_SPLIT ? d->p1_split : d->p1_il) : 0;
     c.p2 = same ? d->p2 : 0;
+    c.pf = env_int("FFTC_PF", same ? d->pf : 0);
     // FFTC_PIPE4: bit 0 forces the pass-1 feed on or off (code FFTC_TUNE_P1_PIPE, default
     // tensor-map boxes with two buffers), bit 1 the pass-2 feed (FFTC_TUNE_P2_PIPE)
     const int force = env_int("FFTC_PIPE4", -1);
@@ -182,7 +185,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     }
 
     // four-step: n = M * K
-    int logm, e1, e2, c1 = kPassLines, c2 = kPassLines, p1code = 0, p2code = 0;
+    int logm, e1, e2, c1 = kPassLines, c2 = kPassLines, p1code = 0, p2code = 0, pf = 0;
     if (tc) {
         logm = p->logn / 2;
         e1 = e2 = 4;
@@ -195,6 +198,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         c2 = fc.c2;
         p1code = fc.p1;
         p2code = fc.p2;
+        pf = fc.pf;
     }
     const int logk = p->logn - logm;
     const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
@@ -268,6 +272,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         b.tw2_full = p->tw2_full;
         b.log_n2 = p->logn;
         b.tw2_lo_bits = p->tw2_lo_bits;
+        b.pf_tiles = pf ? -1 : 0;
         fftc_status s = upload_stage_tables(p, pp);
         if (s != FFTC_OK) return s;
         if ((s = prepare(pp)) != FFTC_OK) return s;

@@ -87,6 +87,7 @@ bool choose_rows(int logn, int lin, int *loge, int *lines);
 struct FourStepChoice {
     int logm, e1, c1, e2, c2;
     int p1, p2;  // pipe codes of the two passes (0: plain kernel)
+    int pf;      // plain pass 1 prefetches the next wave's input into L2
 };
 FourStepChoice choose_four_step(int logn, int lay);
 
