@@ -57,6 +57,47 @@ def weak_scaling_value(world: int, step_flops: float, steps: int, ms: float) -> 
     return world * step_flops * steps / (ms * 1e-3) / 1e9
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_2308_00497_gb300", "csrc")
+
+
+def csrc_digest() -> str:
+    """SHA-256 over the kernel sources (names and bytes), to tell whether a stored ncu
+    capture still describes the kernels that run."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def stored_traffic(kind: str):
+    """DRAM bytes per launch of a kernel kind from the committed ncu summary
+    (dram__bytes_read.sum + dram__bytes_write.sum), or None when the summary is missing
+    or was taken on kernel sources other than the current ones."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    digest, table = None, {}
+    for ln in lines:
+        if ln.startswith("csrc_sha256:"):
+            digest = ln.split(":", 1)[1].strip()
+        elif ln and not ln.startswith("#") and len(ln.split()) >= 2:
+            k, v = ln.split()[:2]
+            try:
+                table[k] = float(v)
+            except ValueError:
+                pass
+    if digest != csrc_digest():
+        return None
+    return table.get(kind)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -302,7 +343,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None, "bytes_per_launch": bytes_per_launch,
+                         "traffic": stored_traffic(dom), "bytes_per_launch": bytes_per_launch,
                          "avg_launch_ms": round(dom_avg_ms, 5), "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()}},
             "cpu_baseline": cpu,
             "e2e": e2e,
