@@ -92,8 +92,11 @@ fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream
 /*
  * Same transforms, with HOST buffers: copies `host_in` to `dev_buf` (a caller-owned
  * device buffer of at least fftc_plan_bytes() bytes), transforms it in place, copies
- * the result to `host_out`, and waits for the stream. Host buffers should be pinned
- * (page-locked) for the copies to run at full speed. Meant for end-to-end timing.
+ * the result to `host_out`, and waits for the stream. FP32 batches larger than ~32 MiB
+ * travel in chunks of whole transforms, each chunk's copy in, transform and copy out
+ * overlapped with its neighbours' (two copy streams owned by the plan, chained to
+ * `stream` with events). Host buffers should be pinned (page-locked) for the copies to
+ * overlap and run at full speed. `dev_buf` must not be used by other work meanwhile.
  */
 fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_out, void *dev_buf,
                               void *stream);

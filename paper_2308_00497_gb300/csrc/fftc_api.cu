@@ -309,14 +309,7 @@ fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_ou
     if (plan->total_elems == 0) return FFTC_OK;
     if (!host_in || !host_out || !dev_buf) return FFTC_ERR_INVALID_VALUE;
     if (reinterpret_cast<uintptr_t>(dev_buf) & 15) return FFTC_ERR_MISALIGNED;
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = (size_t)plan->total_elems * 8;
-    if (cudaMemcpyAsync(dev_buf, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FFTC_ERR_CUDA;
-    fftc_status s = plan_run(plan, dev_buf, dev_buf, nullptr, 0.f, st);
-    if (s != FFTC_OK) return s;
-    if (cudaMemcpyAsync(host_out, dev_buf, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return FFTC_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return FFTC_ERR_CUDA;
-    return FFTC_OK;
+    return host_execute(plan, host_in, host_out, dev_buf, (cudaStream_t)stream);
 }
 
 fftc_status fftc_stage_twiddles(int logl, int loge, float *out, int64_t capacity, int64_t *count) {

@@ -367,9 +367,43 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     return FFTC_OK;
 }
 
+fftc_status plan_run_range(fftc_plan_s *p, const void *in, void *out, int64_t b0, int64_t nb, cudaStream_t st) {
+    if (p->uneven || p->fs || p->precision != FFTC_FP32 || b0 < 0 || nb < 0 || b0 + nb > p->batch)
+        return FFTC_ERR_INVALID_VALUE;
+    if (nb == 0) return FFTC_OK;
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    // complex offset of transform b0: interleaved buffers count floats in pairs, the split
+    // planes count one float per element (the plane stride stays the whole batch's)
+    const int64_t el = b0 * p->n;
+    const int64_t fo = p->layout == FFTC_LAYOUT_SPLIT ? el : 2 * el;
+    const float *src = (const float *)in + fo;
+    float *dst = (float *)out + fo;
+    PassParams a = p->pass[0].base;
+    a.total_lines = a.total_lines / p->batch * nb;
+    a.in = src;
+    a.conj_in = inv;
+    if (p->npasses == 1) {
+        a.out = dst;
+        a.conj_out = inv;
+        return p->pass[0].k->launch(a, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+    }
+    float *ws = (float *)p->workspace + 2 * el;
+    a.out = ws;
+    a.conj_out = 0;
+    if (p->pass[0].k->launch(a, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    PassParams b = p->pass[1].base;
+    b.total_lines = b.total_lines / p->batch * nb;
+    b.in = ws;
+    b.out = dst;
+    b.conj_in = 0;
+    b.conj_out = inv;
+    return p->pass[1].k->launch(b, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+}
+
 void plan_destroy_extra(fftc_plan_s *p) {
     uneven_free(p);
     fs_free(p);
+    host_free(p);
 }
 
 void plan_probe_free(fftc_plan_s *p) {

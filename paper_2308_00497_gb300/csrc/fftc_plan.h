@@ -50,6 +50,9 @@ struct fftc_plan_s {
     std::vector<cudaEvent_t> probe_events;
     int probe_slots = 0, probe_used = 0;
     bool probe_on = false;
+    // host-buffer execution (fftc_host.cu): copy streams and events, created on first use
+    cudaStream_t xfer_in = nullptr, xfer_out = nullptr;
+    cudaEvent_t xev[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace fftc {
@@ -60,6 +63,12 @@ fftc_status plan_build(fftc_plan_s *p);
 fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
                      cudaStream_t st);
 fftc_status plan_check_errors(fftc_plan_s *p, cudaStream_t st);
+// Enqueue the plan on transforms [b0, b0 + nb) of the batch only (FP32 plans with one or two
+// launched passes); `in` / `out` are the whole-batch buffers.
+fftc_status plan_run_range(fftc_plan_s *p, const void *in, void *out, int64_t b0, int64_t nb, cudaStream_t st);
+// Host buffers in and out, copies overlapped with the transform chunk by chunk (fftc_host.cu)
+fftc_status host_execute(fftc_plan_s *p, const void *host_in, void *host_out, void *dev_buf, cudaStream_t st);
+void host_free(fftc_plan_s *p);
 void plan_destroy_extra(fftc_plan_s *p);
 void plan_probe_free(fftc_plan_s *p);
 void plan_free_device(fftc_plan_s *p);
