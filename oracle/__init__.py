@@ -69,7 +69,7 @@ def _load():
         if _lib is None:
             build_oracle()
             lib = ctypes.CDLL(_LIB_PATH)
-            for name in ("oracle_dft", "oracle_fft_r2"):
+            for name in ("oracle_dft", "oracle_fft_r2", "oracle_fft_mixed"):
                 f = getattr(lib, name)
                 f.restype = ctypes.c_int
                 f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
@@ -109,12 +109,20 @@ def fft_r2(x, inverse: bool = False, threads: int | None = None) -> np.ndarray:
     return _run("oracle_fft_r2", x, inverse, threads)
 
 
+def fft_mixed(x, inverse: bool = False, threads: int | None = None) -> np.ndarray:
+    """Recursive mixed-radix FFT (smallest prime factor first, any n) along the last axis, FP64."""
+    return _run("oracle_fft_mixed", x, inverse, threads)
+
+
 def fft(x, inverse: bool = False, threads: int | None = None) -> np.ndarray:
-    """The oracle transform: direct sum for n <= 4096, radix-2 above."""
+    """The oracle transform: direct sum for n <= 4096, radix-2 above for powers of two,
+    mixed radix above for other n."""
     n = np.asarray(x).shape[-1]
     if n <= DIRECT_MAX_N:
         return dft(x, inverse, threads)
-    return fft_r2(x, inverse, threads)
+    if n & (n - 1) == 0:
+        return fft_r2(x, inverse, threads)
+    return fft_mixed(x, inverse, threads)
 
 
 # ----------------------------------------------------------------------------

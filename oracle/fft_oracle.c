@@ -16,6 +16,10 @@
  *   oracle_fft_r2     recursive radix-2 decimation in time (Eq. 1 with K = 2 applied
  *                     recursively); each twiddle is cos/sin(2*pi*k/n) called
  *                     directly, never obtained by recurrence.
+ *   oracle_fft_mixed  recursive decimation in time by the smallest prime factor p of n
+ *                     (Eq. 1 with K = p, any n >= 1); a prime length is summed directly.
+ *                     Every twiddle angle is reduced exactly in integers and read from
+ *                     one table of cos/sin(2*pi*m/n).
  * Both take and return interleaved doubles: x[b][j][0] = Re, x[b][j][1] = Im.
  * Batches are split across POSIX threads (one transform per task).
  */
@@ -112,6 +116,71 @@ static void r2_rec(int64_t n, int64_t ntop, int sign, const double *x, int64_t s
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* recursive mixed-radix decimation in time (smallest prime first)     */
+/* ------------------------------------------------------------------ */
+
+static int64_t smallest_prime_factor(int64_t n) {
+    if (n % 2 == 0) return 2;
+    for (int64_t f = 3; f * f <= n; f += 2)
+        if (n % f == 0) return f;
+    return n;
+}
+
+/*
+ * out[0..n) <- DFT_n of x[0], x[stride], x[2*stride], ...
+ * With p the smallest prime factor of n and m = n / p, the p decimated subsequences
+ * x[r + p*j] (j < m) are transformed recursively into Y_r (the stride permutation and
+ * I_p (x) DFT_m of Eq. 1), then
+ *     X_k = sum_{r<p} w_n^{r*k} * Y_r[k mod m],   k < n,  w_n = exp(s*2*pi*i/n)
+ * (the twiddle diagonal and DFT_p (x) I_m written as one sum). A prime n is summed
+ * directly. tab holds cos/sin(2*pi*t/ntop) for t < ntop; the angle 2*pi*(r*k mod n)/n is
+ * entry (r*k mod n) * (ntop/n), the same fraction in integers.
+ */
+static int mr_rec(int64_t n, int64_t ntop, int sign, const double *x, int64_t stride, double *out,
+                  const double *tab) {
+    if (n == 1) {
+        out[0] = x[0];
+        out[1] = x[1];
+        return 0;
+    }
+    const int64_t p = smallest_prime_factor(n), m = n / p, step = ntop / n;
+    double *y = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    if (!y) return -3;
+    if (p == n) { /* prime length: the sum over j itself */
+        for (int64_t j = 0; j < n; ++j) {
+            y[2 * j] = x[2 * j * stride];
+            y[2 * j + 1] = x[2 * j * stride + 1];
+        }
+    } else {
+        for (int64_t r = 0; r < p; ++r) {
+            int rc = mr_rec(m, ntop, sign, x + 2 * r * stride, p * stride, y + 2 * r * m, tab);
+            if (rc) {
+                free(y);
+                return rc;
+            }
+        }
+    }
+    /* prime n: Y_r is the single sample x_r (m = 1), so the same combination applies */
+    for (int64_t k = 0; k < n; ++k) {
+        acc_t re = {0.0, 0.0}, im = {0.0, 0.0};
+        const int64_t km = k % m;
+        for (int64_t r = 0; r < p; ++r) {
+            const int64_t t = (int64_t)(((__int128)r * k) % n) * step;
+            const double c = tab[2 * t], sn = sign * tab[2 * t + 1];
+            const double yr = y[2 * (r * m + km)], yi = y[2 * (r * m + km) + 1];
+            acc_add(&re, yr * c);
+            acc_add(&re, -yi * sn);
+            acc_add(&im, yr * sn);
+            acc_add(&im, yi * c);
+        }
+        out[2 * k] = re.sum + re.comp;
+        out[2 * k + 1] = im.sum + im.comp;
+    }
+    free(y);
+    return 0;
+}
+
 /* cos/sin(2*pi*m/n) for m < n/2, each evaluated directly */
 static double *half_circle_table(int64_t n) {
     int64_t h = n / 2 > 0 ? n / 2 : 1;
@@ -130,13 +199,14 @@ static double *half_circle_table(int64_t n) {
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    int kind; /* 0 = direct DFT, 1 = radix-2 */
+    int kind; /* 0 = direct DFT, 1 = radix-2, 2 = mixed radix */
     int64_t n, batch;
     int sign;
     const double *x;
     double *X;
     const double *tab;
     int64_t next;
+    int err;
     pthread_mutex_t mu;
 } job_t;
 
@@ -149,10 +219,15 @@ static void *worker(void *arg) {
         if (b >= J->batch) break;
         const double *x = J->x + 2 * J->n * b;
         double *X = J->X + 2 * J->n * b;
-        if (J->kind == 0)
+        if (J->kind == 0) {
             dft_one(J->n, J->sign, x, X, J->tab);
-        else
+        } else if (J->kind == 1) {
             r2_rec(J->n, J->n, J->sign, x, 1, X, J->tab);
+        } else if (mr_rec(J->n, J->n, J->sign, x, 1, X, J->tab) != 0) {
+            pthread_mutex_lock(&J->mu);
+            J->err = -3;
+            pthread_mutex_unlock(&J->mu);
+        }
     }
     return NULL;
 }
@@ -162,7 +237,7 @@ static int run_batched(int kind, int64_t n, int64_t batch, int sign, const doubl
     if (n < 1 || batch < 0 || (sign != 1 && sign != -1)) return -1;
     if (kind == 1 && (n & (n - 1)) != 0) return -2;
     if (batch == 0) return 0;
-    double *tab = kind == 0 ? unit_circle_table(n) : half_circle_table(n);
+    double *tab = kind == 1 ? half_circle_table(n) : unit_circle_table(n);
     if (!tab) return -3;
     job_t J;
     J.kind = kind;
@@ -173,6 +248,7 @@ static int run_batched(int kind, int64_t n, int64_t batch, int sign, const doubl
     J.X = X;
     J.tab = tab;
     J.next = 0;
+    J.err = 0;
     pthread_mutex_init(&J.mu, NULL);
     if (threads < 1) threads = 1;
     if (threads > batch) threads = (int)batch;
@@ -186,7 +262,7 @@ static int run_batched(int kind, int64_t n, int64_t batch, int sign, const doubl
     free(tid);
     pthread_mutex_destroy(&J.mu);
     free(tab);
-    return 0;
+    return J.err;
 }
 
 /* Direct O(n^2) DFT of `batch` transforms of length n (any n >= 1). Returns 0 on success. */
@@ -197,4 +273,9 @@ int oracle_dft(int64_t n, int64_t batch, int sign, const double *x, double *X, i
 /* Recursive radix-2 FFT of `batch` transforms of length n (a power of two). Returns 0 on success. */
 int oracle_fft_r2(int64_t n, int64_t batch, int sign, const double *x, double *X, int threads) {
     return run_batched(1, n, batch, sign, x, X, threads);
+}
+
+/* Recursive mixed-radix FFT of `batch` transforms of length n (any n >= 1). Returns 0 on success. */
+int oracle_fft_mixed(int64_t n, int64_t batch, int sign, const double *x, double *X, int threads) {
+    return run_batched(2, n, batch, sign, x, X, threads);
 }
