@@ -61,7 +61,9 @@ typedef enum {
 typedef enum {
     FFTC_OK = 0,
     FFTC_ERR_INVALID_VALUE = 1,   /* a NULL pointer, a bad enum, a negative count */
-    FFTC_ERR_UNSUPPORTED_SIZE = 2,/* n not a power of two in [2, 2^20], or batch too large */
+    FFTC_ERR_UNSUPPORTED_SIZE = 2,/* n outside [2, 2^20] or with a prime factor above 7, a
+                                     non-power-of-two n with a tensor-core precision, or
+                                     batch too large */
     FFTC_ERR_MISALIGNED = 3,      /* a data pointer not 16-byte aligned */
     FFTC_ERR_ALLOC = 4,           /* device or host allocation failed in plan creation */
     FFTC_ERR_CUDA = 5,            /* a CUDA runtime call or kernel launch failed */
@@ -70,12 +72,15 @@ typedef enum {
 } fftc_status;
 
 /*
- * Create a plan for `batch` transforms of length n (n = 2^e, 2 <= n <= 2^20), in
- * the given layout, direction and precision, on the current CUDA device.
+ * Create a plan for `batch` transforms of length n, 2 <= n <= 2^20, in the given
+ * layout, direction and precision, on the current CUDA device. n is a power of two,
+ * or (FFTC_FP32 only) any n = 2^a 3^b 5^c 7^d: Eq. 1 with mixed radices 16, 8, 4, 2,
+ * 7, 5 and 3 (the mixed radix the paper names as missing, Sections 4 and 6), one
+ * pass up to n = 8192 and two passes (n = M K) above.
  * Precomputes the twiddle diagonals D (Eq. 1; Table 1 "Mul") in FP64 with exact
  * integer angle reduction and rounds them once to the working precision.
  * Returns NULL on error; fftc_get_last_error() then tells why.
- * Tensor-core precisions require n >= 16.
+ * Tensor-core precisions require a power of two n >= 16.
  */
 fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_direction direction,
                            fftc_precision precision);

@@ -201,7 +201,8 @@ fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_di
     if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_BF16_TC_SPLIT)
         return fail(FFTC_ERR_INVALID_VALUE);
     if (batch < 0) return fail(FFTC_ERR_INVALID_VALUE);
-    if (!is_pow2(n) || n < 2 || n > (int64_t(1) << 20)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    if (n < 2 || n > (int64_t(1) << 20)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    if (!is_pow2(n) && (!mixed_supported(n) || precision != FFTC_FP32)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
     if (batch > (int64_t(1) << 40) / n) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
 
     fftc_plan_s *p = new (std::nothrow) fftc_plan_s();
@@ -249,8 +250,9 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
     } else if (passes) {
         *passes = plan->npasses;
     }
+    if (plan->mixed) cnt = mixed_radix_list(plan, tmp, 32);
     const int nsched = plan->fs ? 2 : plan->npasses;
-    for (int i = 0; i < nsched && !plan->uneven; ++i) {
+    for (int i = 0; i < nsched && !plan->uneven && !plan->mixed; ++i) {
         const PassPlan &pp = plan->pass[i];
         HostSched h = host_sched(pp.logl, pp.loge, plan->precision != FFTC_FP32);
         for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];

@@ -1,0 +1,282 @@
+// Host side of the mixed-radix path (n = 2^a 3^b 5^c 7^d, not a power of two): radix
+// factorisation, single pass up to kMixedSinglePass elements, Eq. 1 once at the HBM level
+// (n = M K, both factors at most kMixedSinglePass) above, FP64-built stage tables and
+// inter-pass diagonal, and the launches (kernels in fftc_mixed.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fftc_mixed.cuh"
+#include "fftc_plan.h"
+
+namespace fftc {
+
+static const int kMixedSinglePass = 8192;  // longest line one CTA transforms (2 x 64 KB)
+static const int kMixedTile = 4096;        // elements per CTA tile for shorter lines
+
+typedef void (*MixedKernel)(MixedArgs);
+
+struct MixedPass {
+    MixedArgs args;
+    MixedKernel kernel = nullptr;
+    int smem = 0, threads = 256;
+    int64_t blocks = 0;
+};
+
+struct MixedState {
+    int npasses = 0;
+    MixedPass pass[2];
+};
+
+bool mixed_supported(int64_t n) {
+    if (n < 2 || n > (int64_t(1) << 20)) return false;
+    int64_t m = n;
+    for (int p : {2, 3, 5, 7})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+// radices of a line in stage order: the odd ones first (7, 5, 3: their Ns = 1 writes have
+// odd strides), then the power-of-two remainder (2, 4 or 8), then the radix-16 stages,
+// whose Ns is largest so that consecutive butterflies write consecutive words
+static std::vector<int> mixed_radices(int64_t L) {
+    std::vector<int> r;
+    int64_t m = L;
+    int twos = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++twos;
+    }
+    for (int p : {7, 5, 3})
+        while (m % p == 0) {
+            r.push_back(p);
+            m /= p;
+        }
+    if (twos % 4) r.push_back(1 << (twos % 4));
+    for (int i = 0; i < twos / 4; ++i) r.push_back(16);
+    return r;
+}
+
+static FastDiv make_div(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.l = l;
+    f.m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    return f;
+}
+
+// the division must be exact for every dividend below `limit` (< 2^31): check the ends
+// of the range and a spread of points in between
+static bool check_div(const FastDiv &f, uint64_t limit) {
+    if (limit > (uint64_t(1) << 31)) return false;
+    auto ok = [&](uint64_t n) { return fdiv((uint32_t)n, f) == (uint32_t)(n / f.d); };
+    for (uint64_t n = 0; n < std::min<uint64_t>(limit, 4096); ++n)
+        if (!ok(n)) return false;
+    for (uint64_t n = limit > 4096 ? limit - 4096 : 0; n < limit; ++n)
+        if (!ok(n)) return false;
+    for (uint64_t n = 0; n < limit; n += 1 + limit / 65536)
+        if (!ok(n)) return false;
+    return true;
+}
+
+template <int KIND, int LIN, int LOUT>
+static MixedKernel mixed_kernel(int nt) {
+    return nt == 512 ? &k_mixed<KIND, LIN, LOUT, 512> : &k_mixed<KIND, LIN, LOUT, 256>;
+}
+
+// stage tables of a line: stage s holds w_{Ns r}^{t k} at (t - 1) Ns + k (t < r, k < Ns)
+static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, int C, int kind, int lin, int lout,
+                                    int64_t lpt) {
+    const std::vector<int> rad = mixed_radices(L);
+    if (rad.empty() || (int)rad.size() > kMixedMaxStages) return FFTC_ERR_UNSUPPORTED_SIZE;
+    MixedArgs &a = mp.args;
+    a.L = (int32_t)L;
+    a.C = C;
+    a.nst = (int32_t)rad.size();
+    a.pitch = (int32_t)L + (C > 1 && (L & 1) == 0 ? 1 : 0);  // odd for column access
+    a.lpt = (int32_t)lpt;
+    std::vector<float2> tw;
+    int64_t ns = 1;
+    for (int s = 0; s < a.nst; ++s) {
+        const int r = rad[(size_t)s];
+        a.radix[s] = (int8_t)r;
+        a.ns[s] = (int32_t)ns;
+        a.tw_off[s] = (int32_t)tw.size();
+        a.div_lr[s] = make_div((uint32_t)(L / r));
+        a.div_ns[s] = make_div((uint32_t)ns);
+        if (!check_div(a.div_lr[s], (uint64_t)C * L) || !check_div(a.div_ns[s], (uint64_t)L))
+            return FFTC_ERR_UNSUPPORTED_SIZE;
+        if (ns > 1)
+            for (int t = 1; t < r; ++t)
+                for (int64_t k = 0; k < ns; ++k) {
+                    double c, sn;
+                    unit_root((int64_t)t * k, ns * r, &c, &sn);
+                    tw.push_back(make_float2((float)c, (float)-sn));
+                }
+        ns *= r;
+    }
+    a.div_L = make_div((uint32_t)L);
+    a.div_C = make_div((uint32_t)C);
+    a.div_lpt = make_div((uint32_t)lpt);
+    const uint64_t tile = (uint64_t)C * L;
+    if (!check_div(a.div_L, tile) || !check_div(a.div_C, tile) ||
+        !check_div(a.div_lpt, (uint64_t)a.p.total_lines + (uint64_t)C))
+        return FFTC_ERR_UNSUPPORTED_SIZE;
+    if (!tw.empty()) {
+        void *d = nullptr;
+        if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        a.p.tw = (const float2 *)d;
+    }
+    // 512 threads for tiles of more than 4096 elements (one or two CTAs per SM)
+    const int nt = tile > 4096 ? 512 : 256;
+    mp.threads = nt;
+    if (kind == KIND_ROWS)
+        mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_ROWS, LAYOUT_IL, LAYOUT_IL>(nt)
+                                     : mixed_kernel<KIND_ROWS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt);
+    else if (kind == KIND_COLS)
+        mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_COLS, LAYOUT_IL, LAYOUT_IL>(nt)
+                                     : mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL>(nt);
+    else
+        mp.kernel = lout == LAYOUT_IL ? mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_IL>(nt)
+                                      : mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT>(nt);
+    mp.smem = 2 * C * a.pitch * (int)sizeof(float2);
+    if (mp.smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void *)mp.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mp.smem) !=
+            cudaSuccess)
+        return FFTC_ERR_CUDA;
+    mp.blocks = (a.p.total_lines + C - 1) / C;
+    return FFTC_OK;
+}
+
+static int mixed_lines(int64_t L) { return (int)std::max<int64_t>(1, kMixedTile / L); }
+
+fftc_status mixed_build(fftc_plan_s *p) {
+    if (p->precision != FFTC_FP32) return FFTC_ERR_UNSUPPORTED_SIZE;
+    MixedState *ms = new (std::nothrow) MixedState();
+    if (!ms) return FFTC_ERR_ALLOC;
+    p->mixed = ms;
+    const int64_t n = p->n, B = p->batch;
+    const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
+    const int64_t plane = lay == LAYOUT_SPLIT ? n * B : 0;
+    p->total_elems = n * B;
+    void *d = nullptr;
+    if (plan_alloc(p, 16, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->d_err = (int *)d;
+    if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (n <= kMixedSinglePass) {
+        ms->npasses = p->npasses = 1;
+        MixedPass &mp = ms->pass[0];
+        PassParams &b = mp.args.p;
+        memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
+        b.in_plane = b.out_plane = plane;
+        b.total_lines = B;
+        b.in_tr = b.out_tr = n;
+        b.in_elem = b.out_elem = 1;
+        return mixed_pass_setup(p, mp, n, mixed_lines(n), KIND_ROWS, lay, lay, 1);
+    }
+    // n = M K with both factors at most one CTA's line, M as close to sqrt(n) as possible
+    int64_t M = 0;
+    for (int64_t m = 2; m <= kMixedSinglePass; ++m)
+        if (n % m == 0 && n / m <= kMixedSinglePass &&
+            (M == 0 || std::llabs((long long)(m * m - n)) < std::llabs((long long)(M * M - n))))
+            M = m;
+    if (M == 0) return FFTC_ERR_UNSUPPORTED_SIZE;
+    const int64_t K = n / M;
+    ms->npasses = p->npasses = 2;
+    if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->workspace = (float2 *)d;
+    {  // the inter-pass diagonal D of Eq. 1 in pass-1 order: entry t' K + b = w_N^(b t')
+        std::vector<float2> full((size_t)n);
+        for (int64_t tp = 0; tp < M; ++tp)
+            for (int64_t b = 0; b < K; ++b) {
+                double c, s;
+                unit_root(tp * b, n, &c, &s);
+                full[(size_t)(tp * K + b)] = make_float2((float)c, (float)-s);
+            }
+        if (plan_upload(p, full.data(), full.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        p->tw2_full = (float2 *)d;
+    }
+    {  // pass 1: K columns of length M at stride K, times the diagonal, into the workspace
+        MixedPass &mp = ms->pass[0];
+        PassParams &b = mp.args.p;
+        memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
+        b.in_plane = plane;
+        b.total_lines = B * K;
+        b.in_tr = b.out_tr = n;
+        b.in_line = b.out_line = 1;
+        b.in_elem = b.out_elem = K;
+        b.tw2_full = p->tw2_full;
+        fftc_status s = mixed_pass_setup(p, mp, M, (int)std::min<int64_t>(K, mixed_lines(M)), KIND_COLS, lay,
+                                         LAYOUT_IL, K);
+        if (s != FFTC_OK) return s;
+    }
+    {  // pass 2: M rows of length K, stored transposed (output k1 + M k2)
+        MixedPass &mp = ms->pass[1];
+        PassParams &b = mp.args.p;
+        memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
+        b.out_plane = plane;
+        b.total_lines = B * M;
+        b.in_tr = b.out_tr = n;
+        b.in_line = K;
+        b.in_elem = 1;
+        b.out_line = 1;
+        b.out_elem = M;
+        return mixed_pass_setup(p, mp, K, (int)std::min<int64_t>(M, mixed_lines(K)), KIND_ROWST, LAYOUT_IL, lay, M);
+    }
+}
+
+static cudaError_t mixed_launch(const MixedPass &mp, const MixedArgs &a, cudaStream_t st) {
+    if (mp.blocks <= 0) return cudaSuccess;
+    if (mp.blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    void *kargs[] = {(void *)&a};
+    return cudaLaunchKernel((const void *)mp.kernel, dim3((unsigned)mp.blocks), dim3(mp.threads), kargs,
+                            (size_t)mp.smem, st);
+}
+
+fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st) {
+    const MixedState *ms = p->mixed;
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    if (ms->npasses == 1) {
+        MixedArgs a = ms->pass[0].args;
+        a.p.in = (const float *)in;
+        a.p.out = (float *)out;
+        a.p.conj_in = a.p.conj_out = inv;
+        return mixed_launch(ms->pass[0], a, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+    }
+    MixedArgs a = ms->pass[0].args;
+    a.p.in = (const float *)in;
+    a.p.out = (float *)p->workspace;
+    a.p.conj_in = inv;
+    if (mixed_launch(ms->pass[0], a, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    MixedArgs b = ms->pass[1].args;
+    b.p.in = (const float *)p->workspace;
+    b.p.out = (float *)out;
+    b.p.conj_out = inv;
+    return mixed_launch(ms->pass[1], b, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+}
+
+int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap) {
+    int cnt = 0;
+    for (int i = 0; i < p->mixed->npasses; ++i) {
+        const MixedArgs &a = p->mixed->pass[i].args;
+        for (int s = 0; s < a.nst; ++s)
+            if (cnt < cap) radices[cnt++] = a.radix[s];
+    }
+    return cnt;
+}
+
+void mixed_free(fftc_plan_s *p) {
+    delete p->mixed;
+    p->mixed = nullptr;
+}
+
+}  // namespace fftc

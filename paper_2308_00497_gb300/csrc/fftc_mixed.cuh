@@ -1,0 +1,253 @@
+// Mixed-radix Stockham pass for n = 2^a 3^b 5^c 7^d (not a power of two).
+//
+// One CTA transforms C lines of length L held in shared memory. The radices r_s of the
+// line (from {16, 8, 4, 2, 7, 5, 3}, product L) are runtime values, so one kernel serves
+// every length; each stage s (Ns = r_0 ... r_{s-1}) applies one factor of Eq. 1 to every
+// butterfly group of every line:
+//   read    a[t] = x[j + t L/r]                       (the stride permutation)
+//   twiddle a[t] *= w_{Ns r}^{t (j mod Ns)}            (the diagonal, FP64-built table)
+//   DFT_r   in registers (radix-2 networks for 2..16, paired sums for 3, 5, 7)
+//   write   y[(j / Ns) Ns r + (j mod Ns) + t Ns] = a[t] (autosort)
+// between two shared buffers (ping-pong, one barrier per stage). The tile moves through
+// HBM once: a coalesced load into shared memory, the stages, a coalesced store; the
+// four-step kinds are the same as the power-of-two passes (columns at stride K times the
+// inter-pass diagonal w_N^(b t'), or rows stored transposed), with lines addressed by
+// division by invariant integers instead of shifts.
+#pragma once
+
+#include "fftc_device.cuh"
+#include "fftc_internal.h"
+
+namespace fftc {
+
+constexpr int kMixedMaxStages = 24;
+
+
+// Unsigned division by an invariant d for dividends below 2^31 (the round-up multiply
+// and shift of Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): q = (mulhi(n, m) + n) >> l with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1. The host checks it over the dividends a plan uses.
+struct FastDiv {
+    uint32_t d, m, l;
+};
+
+__host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+#ifdef __CUDA_ARCH__
+    return (__umulhi(n, f.m) + n) >> f.l;
+#else
+    return (uint32_t)((((uint64_t)n * f.m) >> 32) + n) >> f.l;
+#endif
+}
+
+struct MixedArgs {
+    PassParams p;            // buffers, planes, line / element strides, conj, stage table (tw),
+                             // inter-pass diagonal (tw2_full, columns kind), error word
+    int32_t L, C, nst, pitch;
+    int32_t lpt;             // lines per transform (1 rows, K columns, M transposed rows)
+    FastDiv div_lpt, div_L, div_C;
+    int8_t radix[kMixedMaxStages];
+    int32_t ns[kMixedMaxStages], tw_off[kMixedMaxStages];
+    FastDiv div_lr[kMixedMaxStages], div_ns[kMixedMaxStages];
+};
+
+// cos and sin of 2 pi m / r for the odd radices (mathematical constants)
+__host__ __device__ constexpr float mixed_cos(int r, int m) {
+    return r == 3 ? (m == 1 ? -0.5f : -0.5f)
+         : r == 5 ? (m == 1 ? 0.30901699437494742410f : -0.80901699437494742410f)
+                  : (m == 1 ? 0.62348980185873353053f : m == 2 ? -0.22252093395631440429f : -0.90096886790241912624f);
+}
+__host__ __device__ constexpr float mixed_sin(int r, int m) {
+    return r == 3 ? 0.86602540378443864676f
+         : r == 5 ? (m == 1 ? 0.95105651629515357212f : 0.58778525229247312917f)
+                  : (m == 1 ? 0.78183148246802980871f : m == 2 ? 0.97492791218182360702f : 0.43388373911755812048f);
+}
+
+// Forward DFT_R for odd prime R in registers: with a_j = x_j + x_{R-j} and
+// b_j = x_j - x_{R-j} (j = 1 .. (R-1)/2),
+//   X_k     = x_0 + sum_j cos(2 pi jk/R) a_j - i sum_j sin(2 pi jk/R) b_j
+//   X_{R-k} = x_0 + sum_j cos(2 pi jk/R) a_j + i sum_j sin(2 pi jk/R) b_j.
+template <int R>
+__device__ __forceinline__ void dft_odd(float2 *x) {
+    constexpr int H = (R - 1) / 2;
+    float2 a[H + 1], b[H + 1];
+    float2 s0 = x[0];
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+        a[j] = cadd(x[j], x[R - j]);
+        b[j] = csub(x[j], x[R - j]);
+        s0 = cadd(s0, a[j]);
+    }
+    float2 y[R];
+    y[0] = s0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        float2 A = x[0], B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 1; j <= H; ++j) {
+            const int m = (j * k) % R;  // compile-time
+            const float c = m <= H ? mixed_cos(R, m) : mixed_cos(R, R - m);
+            const float s = m <= H ? mixed_sin(R, m) : -mixed_sin(R, R - m);
+            A.x += c * a[j].x;
+            A.y += c * a[j].y;
+            B.x += s * b[j].x;
+            B.y += s * b[j].y;
+        }
+        // -i B = (B.y, -B.x)
+        y[k] = make_float2(A.x + B.y, A.y - B.x);
+        y[R - k] = make_float2(A.x - B.y, A.y + B.x);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = y[k];
+}
+
+template <int R>
+__device__ __forceinline__ void dft_small(float2 *v) {
+    if constexpr ((R & (R - 1)) == 0) dft<R>(v);
+    else dft_odd<R>(v);
+}
+
+template <int R, int NT>
+__device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const float2 *src, float2 *dst) {
+    const int L = a.L, Lr = L / R, Ns = a.ns[s];
+    const int G = a.C * Lr;
+    const float2 *tw = a.p.tw + a.tw_off[s];
+#pragma unroll 2
+    for (int gi = threadIdx.x; gi < G; gi += NT) {
+        const int c = (int)fdiv((uint32_t)gi, a.div_lr[s]);
+        const int j = gi - c * Lr;
+        const float2 *line = src + c * a.pitch;
+        float2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = line[j + t * Lr];
+        const int jq = (int)fdiv((uint32_t)j, a.div_ns[s]);
+        const int jm = j - jq * Ns;
+        if (Ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) v[t] = cmul(v[t], __ldg(tw + (t - 1) * Ns + jm));
+        }
+        dft_small<R>(v);
+        float2 *out = dst + c * a.pitch;
+        const int o = jq * Ns * R + jm;
+#pragma unroll
+        for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
+    }
+}
+
+// Global <-> shared copies of a tile. Element a of tile line c is global line g0 + c,
+// at (g / lpt) * tr + (g mod lpt) * line_stride + a * elem_stride. Element-contiguous
+// lines are walked element-fastest, strided ones line-fastest (both coalesced).
+// a thread keeps kMixedBatch loads in flight before it writes any of them to shared memory
+constexpr int kMixedBatch = 16;
+
+template <int KIND>
+__device__ __forceinline__ void tile_coord(const MixedArgs &a, int f, int &c, int &e) {
+    if constexpr (KIND == KIND_COLS) {
+        e = (int)fdiv((uint32_t)f, a.div_C);
+        c = f - e * a.C;
+    } else {
+        c = (int)fdiv((uint32_t)f, a.div_L);
+        e = f - c * a.L;
+    }
+}
+
+template <int KIND, int LIN, int NT>
+__device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, float2 *sm) {
+    const PassParams &p = a.p;
+    const int T = a.C * a.L;
+    const int cj = p.conj_in;
+    for (int base = 0; base < T; base += NT * kMixedBatch) {
+        float2 x[kMixedBatch];
+#pragma unroll
+        for (int i = 0; i < kMixedBatch; ++i) {
+            const int f = base + i * NT + (int)threadIdx.x;
+            x[i] = make_float2(0.f, 0.f);
+            int c, e;
+            tile_coord<KIND>(a, f, c, e);
+            const int64_t g = g0 + c;
+            if (f < T && g < p.total_lines) {
+                const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
+                const int64_t off = tr * p.in_tr + l * p.in_line + (int64_t)e * p.in_elem;
+                if constexpr (LIN == LAYOUT_IL) {
+                    x[i] = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
+                } else {
+                    x[i].x = __ldcs(p.in + off);
+                    x[i].y = __ldcs(p.in + p.in_plane + off);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kMixedBatch; ++i) {
+            const int f = base + i * NT + (int)threadIdx.x;
+            if (f < T) {
+                int c, e;
+                tile_coord<KIND>(a, f, c, e);
+                if (cj) x[i].y = -x[i].y;
+                sm[c * a.pitch + e] = x[i];
+            }
+        }
+    }
+}
+
+template <int KIND, int LOUT, int NT>
+__device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, const float2 *sm) {
+    const PassParams &p = a.p;
+    const int L = a.L, C = a.C, T = C * L;
+    const int cj = p.conj_out;
+#pragma unroll 4
+    for (int f = threadIdx.x; f < T; f += NT) {
+        int c, e;
+        if constexpr (KIND == KIND_ROWS) {
+            c = (int)fdiv((uint32_t)f, a.div_L);
+            e = f - c * L;
+        } else {
+            e = (int)fdiv((uint32_t)f, a.div_C);
+            c = f - e * C;
+        }
+        const int64_t g = g0 + c;
+        if (g >= p.total_lines) continue;
+        const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
+        float2 x = sm[c * a.pitch + e];
+        if constexpr (KIND == KIND_COLS) {
+            // inter-pass diagonal of Eq. 1: column l, output row e: w_N^(l e)
+            x = cmul(x, __ldg(p.tw2_full + (int64_t)e * a.lpt + l));
+        }
+        if (cj) x.y = -x.y;
+        const int64_t off = tr * p.out_tr + l * p.out_line + (int64_t)e * p.out_elem;
+        if constexpr (KIND == KIND_COLS) {
+            __stcg(reinterpret_cast<float2 *>(p.out) + off, x);  // workspace: keep it in L2
+        } else if constexpr (LOUT == LAYOUT_IL) {
+            __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
+        } else {
+            __stcs(p.out + off, x.x);
+            __stcs(p.out + p.out_plane + off, x.y);
+        }
+    }
+}
+
+template <int KIND, int LIN, int LOUT, int NT>
+__global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs a) {
+    extern __shared__ float2 sm_mixed[];
+    float2 *buf0 = sm_mixed, *buf1 = sm_mixed + a.C * a.pitch;
+    const int64_t g0 = (int64_t)blockIdx.x * a.C;
+    mixed_load<KIND, LIN, NT>(a, g0, buf0);
+    __syncthreads();
+    float2 *src = buf0, *dst = buf1;
+    for (int s = 0; s < a.nst; ++s) {
+        switch (a.radix[s]) {
+            case 2: mixed_stage<2, NT>(a, s, src, dst); break;
+            case 3: mixed_stage<3, NT>(a, s, src, dst); break;
+            case 4: mixed_stage<4, NT>(a, s, src, dst); break;
+            case 5: mixed_stage<5, NT>(a, s, src, dst); break;
+            case 7: mixed_stage<7, NT>(a, s, src, dst); break;
+            case 8: mixed_stage<8, NT>(a, s, src, dst); break;
+            default: mixed_stage<16, NT>(a, s, src, dst); break;
+        }
+        __syncthreads();
+        float2 *t = src;
+        src = dst;
+        dst = t;
+    }
+    mixed_store<KIND, LOUT, NT>(a, g0, src);
+}
+
+}  // namespace fftc

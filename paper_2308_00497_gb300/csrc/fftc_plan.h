@@ -23,6 +23,7 @@ struct PassPlan {
 struct UnevenState;  // persistent uneven-batch executor (fftc_uneven.cu)
 struct FsState;      // L2-resident four-step executor (fftc_fourstep_l2.cu)
 struct TcState;      // tensor-core radix-16 executor (fftc_tc.cu)
+struct MixedState;   // mixed-radix passes (fftc_mixed.cu)
 
 }  // namespace fftc
 
@@ -45,6 +46,7 @@ struct fftc_plan_s {
     fftc::UnevenState *uneven = nullptr;
     fftc::TcState *tc = nullptr;
     fftc::FsState *fs = nullptr;
+    fftc::MixedState *mixed = nullptr;  // n with factors 3, 5 or 7 (fftc_mixed.cu)
     std::vector<void *> dev_allocs;
     // timing probe: events[slot * 3 + i] before pass i (i < npasses) and after the last
     std::vector<cudaEvent_t> probe_events;
@@ -83,6 +85,13 @@ fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const 
 fftc_status uneven_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
 void uneven_free(fftc_plan_s *p);
 int uneven_max_logn(const fftc_plan_s *p);
+
+// mixed radix, n = 2^a 3^b 5^c 7^d not a power of two (fftc_mixed.cu)
+bool mixed_supported(int64_t n);
+fftc_status mixed_build(fftc_plan_s *p);
+fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
+int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap);
+void mixed_free(fftc_plan_s *p);
 
 // L2-resident four-step (fftc_fourstep_l2.cu)
 bool fs_available(int logn, int lay);

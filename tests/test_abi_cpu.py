@@ -43,10 +43,18 @@ def test_status_strings(lib):
     assert nat.status_string(99) == "FFTC_ERR_UNKNOWN"
 
 
-@pytest.mark.parametrize("n", [0, 1, 3, 12, 1000, 1 << 21, -8])
+@pytest.mark.parametrize("n", [0, 1, 11, 22, 143, 1 << 21, 3 << 19, -8])
 def test_unsupported_sizes_rejected_before_any_device_call(lib, n):
+    """Lengths outside [2, 2^20] or with a prime factor above 7."""
     from paper_2308_00497_gb300 import _native as nat
     assert not lib.fftc_plan_create(n, 4, 0, -1, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3, 4])
+def test_mixed_radix_sizes_are_fp32_only(lib, precision):
+    from paper_2308_00497_gb300 import _native as nat
+    assert not lib.fftc_plan_create(12, 4, 0, -1, precision)
     assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
 
 

@@ -82,3 +82,28 @@ def test_bad_arguments(lib):
     buf = np.zeros(2, np.float32)
     assert lib.fftc_stage_twiddles(10, 5, buf.ctypes.data, 1, ctypes.byref(cnt)) != 0  # too small
     assert cnt.value == 31 * 32
+
+
+def test_odd_radix_constants_in_the_mixed_kernel():
+    """The cos / sin literals of the radix-3, -5 and -7 butterflies are cos(2 pi m / r)
+    and sin(2 pi m / r) (checked against the C library in FP64, then FP32 rounding)."""
+    import math
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2308_00497_gb300", "csrc",
+                            "fftc_mixed.cuh")).read()
+
+    def table(fn):
+        body = src[src.index(f"constexpr float {fn}(int r, int m)"):]
+        body = body[:body.index("}")]
+        return [float(v) for v in re.findall(r"(-?\d+\.\d+)f", body)]
+
+    cos_vals, sin_vals = table("mixed_cos"), table("mixed_sin")
+    # literal order in the source: r = 3 (m = 1, twice), r = 5 (m = 1, 2), r = 7 (m = 1, 2, 3)
+    want_cos = [math.cos(2 * math.pi / 3)] * 2 + [math.cos(2 * math.pi * m / 5) for m in (1, 2)] + \
+               [math.cos(2 * math.pi * m / 7) for m in (1, 2, 3)]
+    want_sin = [math.sin(2 * math.pi / 3)] + [math.sin(2 * math.pi * m / 5) for m in (1, 2)] + \
+               [math.sin(2 * math.pi * m / 7) for m in (1, 2, 3)]
+    assert len(cos_vals) == len(want_cos) and len(sin_vals) == len(want_sin)
+    for got, want in zip(cos_vals + sin_vals, want_cos + want_sin):
+        assert abs(got - want) <= 1e-15, (got, want)
