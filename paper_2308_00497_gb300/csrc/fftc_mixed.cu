@@ -40,24 +40,39 @@ bool mixed_supported(int64_t n) {
     return m == 1;
 }
 
-// radices of a line in stage order: the odd ones first (7, 5, 3: their Ns = 1 writes have
-// odd strides), then the power-of-two remainder (2, 4 or 8), then the radix-16 stages,
-// whose Ns is largest so that consecutive butterflies write consecutive words
+// Radices of a line in stage order, at most 16 (a butterfly's values stay in registers):
+// 3 x 5 = 15 and 3 x 3 = 9 first, then the remaining 3, 5, 7, the power-of-two remainder
+// (2, 4 or 8), folded into one leftover odd factor where the product stays <= 16 (6, 10,
+// 14, 12), and the radix-16 stages last, where Ns is largest.
 static std::vector<int> mixed_radices(int64_t L) {
-    std::vector<int> r;
+    int e[8] = {0};
     int64_t m = L;
-    int twos = 0;
-    while (m % 2 == 0) {
-        m /= 2;
-        ++twos;
+    for (int p : {2, 3, 5, 7})
+        while (m % p == 0) {
+            m /= p;
+            ++e[p];
+        }
+    std::vector<int> odd;
+    while (e[3] >= 1 && e[5] >= 1) {
+        odd.push_back(15);
+        --e[3];
+        --e[5];
+    }
+    while (e[3] >= 2) {
+        odd.push_back(9);
+        e[3] -= 2;
     }
     for (int p : {7, 5, 3})
-        while (m % p == 0) {
-            r.push_back(p);
-            m /= p;
+        for (; e[p] > 0; --e[p]) odd.push_back(p);
+    int rem = 1 << (e[2] % 4);
+    for (size_t i = 0; i < odd.size() && rem > 1; ++i)
+        if ((odd[i] == 3 || odd[i] == 5 || odd[i] == 7) && odd[i] * rem <= 16) {
+            odd[i] *= rem;
+            rem = 1;
         }
-    if (twos % 4) r.push_back(1 << (twos % 4));
-    for (int i = 0; i < twos / 4; ++i) r.push_back(16);
+    std::vector<int> r = odd;
+    if (rem > 1) r.push_back(rem);
+    for (int i = 0; i < e[2] / 4; ++i) r.push_back(16);
     return r;
 }
 

@@ -1,12 +1,14 @@
 // Mixed-radix Stockham pass for n = 2^a 3^b 5^c 7^d (not a power of two).
 //
 // One CTA transforms C lines of length L held in shared memory. The radices r_s of the
-// line (from {16, 8, 4, 2, 7, 5, 3}, product L) are runtime values, so one kernel serves
+// line (from {16, 15, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2}, product L) are runtime values,
+// so one kernel serves
 // every length; each stage s (Ns = r_0 ... r_{s-1}) applies one factor of Eq. 1 to every
 // butterfly group of every line:
 //   read    a[t] = x[j + t L/r]                       (the stride permutation)
 //   twiddle a[t] *= w_{Ns r}^{t (j mod Ns)}            (the diagonal, FP64-built table)
-//   DFT_r   in registers (radix-2 networks for 2..16, paired sums for 3, 5, 7)
+//   DFT_r   in registers (radix-2 networks for powers of two, paired sums for 3, 5, 7,
+//           and Eq. 1 once more with compile-time twiddles for composite r)
 //   write   y[(j / Ns) Ns r + (j mod Ns) + t Ns] = a[t] (autosort)
 // between two shared buffers (ping-pong, one barrier per stage). The tile moves through
 // HBM once: a coalesced load into shared memory, the stages, a coalesced store; the
@@ -15,6 +17,7 @@
 // division by invariant integers instead of shifts.
 #pragma once
 
+#include "fftc_ctrig.h"
 #include "fftc_device.cuh"
 #include "fftc_internal.h"
 
@@ -100,10 +103,74 @@ __device__ __forceinline__ void dft_odd(float2 *x) {
     for (int k = 0; k < R; ++k) x[k] = y[k];
 }
 
+__host__ __device__ constexpr int ct_spf(int r) { return r % 2 == 0 ? 2 : r % 3 == 0 ? 3 : r % 5 == 0 ? 5 : r % 7 == 0 ? 7 : r; }
+
+// x *= w_R^e (forward, w_R = exp(-2 pi i / R)) with a compile-time exponent: quarter turns
+// exactly, other angles from the compile-time cos / sin
+template <int R, int E>
+__device__ __forceinline__ float2 mul_wr(float2 x) {
+    constexpr int e = E % R;
+    if constexpr (e == 0) {
+        return x;
+    } else if constexpr ((4 * e) % R == 0) {
+        constexpr int q = 4 * e / R;  // quarter turns
+        if constexpr (q == 1) return make_float2(x.y, -x.x);
+        else if constexpr (q == 2) return make_float2(-x.x, -x.y);
+        else return make_float2(-x.y, x.x);
+    } else {
+        constexpr float c = (float)ct_cos(e, R), s = (float)ct_sin(e, R);
+        return make_float2(x.x * c + x.y * s, x.y * c - x.x * s);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void dft_small(float2 *v);
+
+// DFT_R for composite R = P Q in registers (Eq. 1 once more): input j = a + P b; the Q-point
+// DFTs over b for every a, the twiddles w_R^(a q), then the P-point DFTs over a, giving
+// output q + Q k
+template <int P, int Q, int A, int q = 0>
+__device__ __forceinline__ void ct_scatter(float2 *v, const float2 *t) {
+    if constexpr (q < Q) {
+        v[A + P * q] = mul_wr<P * Q, A * q>(t[q]);
+        ct_scatter<P, Q, A, q + 1>(v, t);
+    }
+}
+
+template <int P, int Q, int A = 0>
+__device__ __forceinline__ void ct_inner(float2 *v) {
+    if constexpr (A < P) {
+        float2 t[Q];
+#pragma unroll
+        for (int b = 0; b < Q; ++b) t[b] = v[A + P * b];
+        dft_small<Q>(t);
+        ct_scatter<P, Q, A>(v, t);
+        ct_inner<P, Q, A + 1>(v);
+    }
+}
+
+template <int P, int Q>
+__device__ __forceinline__ void dft_ct(float2 *v) {
+    ct_inner<P, Q>(v);
+    float2 y[P * Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 u[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) u[a] = v[a + P * q];
+        dft_small<P>(u);
+#pragma unroll
+        for (int k = 0; k < P; ++k) y[q + Q * k] = u[k];
+    }
+#pragma unroll
+    for (int i = 0; i < P * Q; ++i) v[i] = y[i];
+}
+
 template <int R>
 __device__ __forceinline__ void dft_small(float2 *v) {
     if constexpr ((R & (R - 1)) == 0) dft<R>(v);
-    else dft_odd<R>(v);
+    else if constexpr (ct_spf(R) == R) dft_odd<R>(v);
+    else dft_ct<ct_spf(R), R / ct_spf(R)>(v);
 }
 
 template <int R, int NT>
@@ -239,7 +306,13 @@ __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs 
             case 4: mixed_stage<4, NT>(a, s, src, dst); break;
             case 5: mixed_stage<5, NT>(a, s, src, dst); break;
             case 7: mixed_stage<7, NT>(a, s, src, dst); break;
+            case 6: mixed_stage<6, NT>(a, s, src, dst); break;
             case 8: mixed_stage<8, NT>(a, s, src, dst); break;
+            case 9: mixed_stage<9, NT>(a, s, src, dst); break;
+            case 10: mixed_stage<10, NT>(a, s, src, dst); break;
+            case 12: mixed_stage<12, NT>(a, s, src, dst); break;
+            case 14: mixed_stage<14, NT>(a, s, src, dst); break;
+            case 15: mixed_stage<15, NT>(a, s, src, dst); break;
             default: mixed_stage<16, NT>(a, s, src, dst); break;
         }
         __syncthreads();

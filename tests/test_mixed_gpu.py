@@ -89,7 +89,7 @@ def test_plan_info_radices_multiply_to_n():
     import paper_2308_00497_gb300 as fc
     for n, passes in ((360, 1), (100000, 2)):
         got, radices = fc.Plan(n, 2).info()
-        assert got == passes and int(np.prod(radices)) == n and set(radices) <= {2, 3, 4, 5, 7, 8, 16}
+        assert got == passes and int(np.prod(radices)) == n and set(radices) <= {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16}
 
 
 def test_pointwise_is_refused_for_mixed_sizes():

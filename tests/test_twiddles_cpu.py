@@ -107,3 +107,28 @@ def test_odd_radix_constants_in_the_mixed_kernel():
     assert len(cos_vals) == len(want_cos) and len(sin_vals) == len(want_sin)
     for got, want in zip(cos_vals + sin_vals, want_cos + want_sin):
         assert abs(got - want) <= 1e-15, (got, want)
+
+
+def test_compile_time_trig_of_the_composite_butterflies(tmp_path):
+    """ct_cos / ct_sin (fftc_ctrig.h, the constants inside the composite-radix butterflies)
+    equal cos / sin(2 pi m / N) to 1e-15 for every N <= 32 and m < N."""
+    import math
+    import os
+    import subprocess
+    hdr = os.path.abspath(os.path.join(os.path.dirname(__file__), "..", "paper_2308_00497_gb300", "csrc"))
+    src = tmp_path / "t.cpp"
+    src.write_text('#include <cstdio>\n#include "fftc_ctrig.h"\nint main(){for(int N=1;N<=32;++N)'
+                   'for(int m=-N;m<2*N;++m)std::printf("%d %d %.17g %.17g\\n",m,N,fftc::ct_cos(m,N),'
+                   'fftc::ct_sin(m,N));}\n')
+    exe = tmp_path / "t"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", hdr, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = [ln.split() for ln in out if ln]
+    assert len(rows) == sum(3 * N for N in range(1, 33))
+    for m, N, c, s in rows:
+        # reference angle folded into [0, pi] exactly first (the argument rounding of an
+        # unfolded 2 pi m / N near 2 pi alone costs ~1e-15)
+        mm, n = int(m) % int(N), int(N)
+        k, sgn = (n - mm, -1.0) if 2 * mm > n else (mm, 1.0)
+        ang = 2 * math.pi * k / n
+        assert abs(float(c) - math.cos(ang)) <= 1e-15 and abs(float(s) - sgn * math.sin(ang)) <= 1e-15, (m, N)
