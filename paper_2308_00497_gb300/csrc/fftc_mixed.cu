@@ -114,7 +114,8 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     a.L = (int32_t)L;
     a.C = C;
     a.nst = (int32_t)rad.size();
-    a.pitch = (int32_t)L + (C > 1 && (L & 1) == 0 ? 1 : 0);  // odd for column access
+    // single pass: lines back to back (flat copies); four-step: an odd pitch for column access
+    a.pitch = (int32_t)L + (kind != KIND_ROWS && C > 1 && (L & 1) == 0 ? 1 : 0);
     a.lpt = (int32_t)lpt;
     std::vector<float2> tw;
     int64_t ns = 1;
@@ -160,7 +161,7 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     else
         mp.kernel = lout == LAYOUT_IL ? mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_IL>(nt)
                                       : mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT>(nt);
-    mp.smem = 2 * C * a.pitch * (int)sizeof(float2);
+    mp.smem = (((C * a.pitch + 1) & ~1) + C * a.pitch) * (int)sizeof(float2);
     if (mp.smem > 48 * 1024 &&
         cudaFuncSetAttribute((const void *)mp.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mp.smem) !=
             cudaSuccess)
@@ -194,7 +195,10 @@ fftc_status mixed_build(fftc_plan_s *p) {
         b.total_lines = B;
         b.in_tr = b.out_tr = n;
         b.in_elem = b.out_elem = 1;
-        return mixed_pass_setup(p, mp, n, mixed_lines(n), KIND_ROWS, lay, lay, 1);
+        // a multiple of 4 lines per tile when there are several, so every tile starts 16-byte
+        // aligned in both layouts
+        const int C = mixed_lines(n);
+        return mixed_pass_setup(p, mp, n, C >= 4 ? C / 4 * 4 : C, KIND_ROWS, lay, lay, 1);
     }
     // n = M K with both factors at most one CTA's line, M as close to sqrt(n) as possible
     int64_t M = 0;

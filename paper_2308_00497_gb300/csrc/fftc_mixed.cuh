@@ -217,6 +217,88 @@ __device__ __forceinline__ void tile_coord(const MixedArgs &a, int f, int &c, in
     }
 }
 
+// Single pass: the tile's lines are back to back in HBM and in shared memory (pitch L), so
+// the copy is flat, in 16-byte vectors when the tile starts 16-byte aligned in every plane
+// (always for tiles of 4 or more lines: their line count is a multiple of 4).
+template <int LAY, int NT, bool LOAD>
+__device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, float2 *sm) {
+    const PassParams &p = a.p;
+    const int64_t lines = min((int64_t)a.C, p.total_lines - g0);
+    const int T = (int)lines * a.L;
+    const int64_t base = g0 * a.L;  // element offset of the tile (in_tr = out_tr = L)
+    const int cj = LOAD ? p.conj_in : p.conj_out;
+    constexpr int V = LAY == LAYOUT_IL ? 2 : 4;  // elements per 16-byte vector and plane
+    int done = 0;
+    const int64_t plane = LAY == LAYOUT_IL ? 0 : (LOAD ? p.in_plane : p.out_plane);
+    if (((base | plane) & (V - 1)) == 0) {
+        const int nv = T / V;
+        if constexpr (LAY == LAYOUT_IL) {
+            float4 *g = reinterpret_cast<float4 *>((LOAD ? const_cast<float *>(p.in) : p.out) + 2 * base);
+            float4 *sv = reinterpret_cast<float4 *>(sm);
+#pragma unroll 8
+            for (int u = threadIdx.x; u < nv; u += NT) {
+                if constexpr (LOAD) {
+                    float4 q = __ldcs(g + u);
+                    if (cj) {
+                        q.y = -q.y;
+                        q.w = -q.w;
+                    }
+                    sv[u] = q;
+                } else {
+                    float4 q = sv[u];
+                    if (cj) {
+                        q.y = -q.y;
+                        q.w = -q.w;
+                    }
+                    __stcs(g + u, q);
+                }
+            }
+        } else {
+            float *pl = LOAD ? const_cast<float *>(p.in) : p.out;
+            float4 *gr = reinterpret_cast<float4 *>(pl + base), *gi = reinterpret_cast<float4 *>(pl + plane + base);
+#pragma unroll 4
+            for (int u = threadIdx.x; u < nv; u += NT) {
+                float2 *e = sm + 4 * u;
+                if constexpr (LOAD) {
+                    const float4 r = __ldcs(gr + u), i = __ldcs(gi + u);
+                    const float sg = cj ? -1.f : 1.f;
+                    e[0] = make_float2(r.x, sg * i.x);
+                    e[1] = make_float2(r.y, sg * i.y);
+                    e[2] = make_float2(r.z, sg * i.z);
+                    e[3] = make_float2(r.w, sg * i.w);
+                } else {
+                    const float sg = cj ? -1.f : 1.f;
+                    __stcs(gr + u, make_float4(e[0].x, e[1].x, e[2].x, e[3].x));
+                    __stcs(gi + u, make_float4(sg * e[0].y, sg * e[1].y, sg * e[2].y, sg * e[3].y));
+                }
+            }
+        }
+        done = nv * V;
+    }
+    for (int f = done + (int)threadIdx.x; f < T; f += NT) {  // unaligned tile or vector tail
+        if constexpr (LOAD) {
+            float2 x;
+            if constexpr (LAY == LAYOUT_IL) {
+                x = __ldcs(reinterpret_cast<const float2 *>(p.in) + base + f);
+            } else {
+                x.x = __ldcs(p.in + base + f);
+                x.y = __ldcs(p.in + p.in_plane + base + f);
+            }
+            if (cj) x.y = -x.y;
+            sm[f] = x;
+        } else {
+            float2 x = sm[f];
+            if (cj) x.y = -x.y;
+            if constexpr (LAY == LAYOUT_IL) {
+                __stcs(reinterpret_cast<float2 *>(p.out) + base + f, x);
+            } else {
+                __stcs(p.out + base + f, x.x);
+                __stcs(p.out + p.out_plane + base + f, x.y);
+            }
+        }
+    }
+}
+
 template <int KIND, int LIN, int NT>
 __device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, float2 *sm) {
     const PassParams &p = a.p;
@@ -294,9 +376,11 @@ __device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, cons
 template <int KIND, int LIN, int LOUT, int NT>
 __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs a) {
     extern __shared__ float2 sm_mixed[];
-    float2 *buf0 = sm_mixed, *buf1 = sm_mixed + a.C * a.pitch;
+    // the second buffer starts 16-byte aligned (the single-pass copies move 16-byte vectors)
+    float2 *buf0 = sm_mixed, *buf1 = sm_mixed + ((a.C * a.pitch + 1) & ~1);
     const int64_t g0 = (int64_t)blockIdx.x * a.C;
-    mixed_load<KIND, LIN, NT>(a, g0, buf0);
+    if constexpr (KIND == KIND_ROWS) rows_copy<LIN, NT, true>(a, g0, buf0);
+    else mixed_load<KIND, LIN, NT>(a, g0, buf0);
     __syncthreads();
     float2 *src = buf0, *dst = buf1;
     for (int s = 0; s < a.nst; ++s) {
@@ -320,7 +404,8 @@ __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs 
         src = dst;
         dst = t;
     }
-    mixed_store<KIND, LOUT, NT>(a, g0, src);
+    if constexpr (KIND == KIND_ROWS) rows_copy<LOUT, NT, false>(a, g0, src);
+    else mixed_store<KIND, LOUT, NT>(a, g0, src);
 }
 
 }  // namespace fftc
