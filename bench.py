@@ -426,9 +426,39 @@ def run_extras(args, dev) -> dict:
                               "fwd_bwd_ms": round(t_fb, 4), "fft_ms": round(t_fft, 4),
                               "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
     del xs, ts, xf
+    out["mixed_radix"] = run_mixed(dev, reps)
     if not args.no_precision:
         out["precision"] = run_precision(args, dev, reps)
     return out
+
+
+MIXED_SIZES = [12, 96, 360, 1000, 3072, 6000, 10000, 59049, 100000, 1000000]
+
+
+def run_mixed(dev, reps: int) -> dict:
+    """n = 2^a 3^b 5^c 7^d (not powers of two), batch = 2^26 // n, forward, both layouts:
+    ms, GFLOP/s (5 n log2 n convention) and the strict HBM fraction (16 B per element)."""
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    res = []
+    xbuf = torch.randn(2 * ELEMS, device=dev)
+    ybuf = torch.empty_like(xbuf)
+    for n in MIXED_SIZES:
+        B = ELEMS // n
+        for layout in LAYOUTS:
+            if layout == "interleaved":
+                x = xbuf[:2 * n * B].view(torch.complex64).view(B, n)
+                y = ybuf[:2 * n * B].view(torch.complex64).view(B, n)
+            else:
+                x, y = xbuf[:2 * n * B].view(2, B, n), ybuf[:2 * n * B].view(2, B, n)
+            p = fc.Plan(n, B, layout, False, device=dev)
+            t = _time_ms(lambda: p.execute(x, y), reps)
+            res.append({"n": n, "batch": B, "layout": layout, "passes": p.info()[0], "ms": round(t, 4),
+                        "gflops": round(flops(n, B) / (t * 1e-3) / 1e9, 1),
+                        "hbm_frac_strict": round(16.0 * n * B / (t * 1e-3) / 1e9 / peaks()[0], 4)})
+    return {"workload": "mixed-radix n (factors 2, 3, 5, 7), n*batch ~ 2^26, forward, interleaved + split",
+            "results": res}
 
 
 def run_precision(args, dev, reps: int) -> dict:
