@@ -125,6 +125,20 @@ def fft(x, inverse: bool = False, threads: int | None = None) -> np.ndarray:
     return fft_mixed(x, inverse, threads)
 
 
+def fftn(x, rank: int, inverse: bool = False, threads: int | None = None) -> np.ndarray:
+    """Multidimensional DFT over the last `rank` axes of x ([batch, d0, ..., d_{rank-1}]):
+    X[k0..] = sum_j x[j0..] prod_a exp(s 2 pi i j_a k_a / d_a), i.e. the 1D oracle applied
+    along each of those axes in turn (the Kronecker product of the 1D DFT matrices, the
+    (F (x) I)(I (x) F) form of Section 3 with both factors full transforms)."""
+    y = np.asarray(x, dtype=np.complex128)
+    for ax in range(y.ndim - rank, y.ndim):
+        moved = np.moveaxis(y, ax, -1)
+        shape = moved.shape
+        flat = fft(np.ascontiguousarray(moved).reshape(-1, shape[-1]), inverse, threads)
+        y = np.moveaxis(flat.reshape(shape), -1, ax)
+    return np.ascontiguousarray(y)
+
+
 # ----------------------------------------------------------------------------
 # batched spectral filter (the differentiation workload)
 # ----------------------------------------------------------------------------
