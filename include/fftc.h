@@ -136,6 +136,21 @@ const char *fftc_status_string(fftc_status s);
 fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices);
 
 /*
+ * Multidimensional transforms: `batch` arrays of rank 2 or 3, dims[0] x ... x dims[rank-1]
+ * stored row-major (the last axis contiguous), array b at element offset b * prod(dims);
+ * the split layout keeps one real plane and one imaginary plane for the whole batch.
+ * X[k] = sum_j x[j] prod_a exp(s 2 pi i j_a k_a / dims[a]) (no normalisation), i.e. the
+ * Kronecker product of the 1D transforms, the (F (x) I)(I (x) F) form of Section 3 with
+ * both factors whole DFTs: the last axis by a 1D plan (any length fftc_plan_create
+ * accepts), every other axis by an in-place strided pass (length 2..8192 with prime
+ * factors 2, 3, 5, 7). FFTC_FP32 only; at most 2^30 elements. Executed with
+ * fftc_execute (in place allowed); fftc_plan_info reports the HBM pass count and no
+ * radices. Returns NULL on error (fftc_get_last_error tells why).
+ */
+fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc_layout layout,
+                              fftc_direction direction, fftc_precision precision);
+
+/*
  * Uneven batch: `count` transforms, row i of length n[i] (a power of two, 64..2^16)
  * with direction[i] in {-1, +1}, stored back to back at complex-element offset
  * offset[i] in the input and output buffers (rows must not overlap). One execute is

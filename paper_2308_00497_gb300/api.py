@@ -156,6 +156,36 @@ class UnevenPlan(Plan):
                              f"on {self.device}")
 
 
+class NdPlan(Plan):
+    """`batch` arrays of rank 2 or 3 with shape `dims`, row-major (fftc_plan_create_nd).
+
+    Interleaved tensors are complex64 [batch, *dims]; split tensors float32 [2, batch, *dims].
+    """
+
+    def __init__(self, dims, batch: int, layout: str = "interleaved", inverse: bool = False, device=None):
+        import numpy as np
+        lib = nat.load()
+        self.dims = tuple(int(d) for d in dims)
+        if len(self.dims) not in (2, 3):
+            raise ValueError("dims must have 2 or 3 entries")
+        self.batch, self.layout, self.inverse, self.precision = int(batch), layout, bool(inverse), "fp32"
+        self.n = int(np.prod(self.dims))
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        d = np.ascontiguousarray(self.dims, dtype=np.int64)
+        with torch.cuda.device(self.device):
+            h = lib.fftc_plan_create_nd(len(self.dims), d.ctypes.data, self.batch, nat.LAYOUTS[layout],
+                                        nat.INVERSE if inverse else nat.FORWARD, nat.FP32)
+        if not h:
+            raise nat.FftcError(lib.fftc_get_last_error(), f"fftc_plan_create_nd(dims={self.dims}, batch={batch})")
+        self._h = ctypes.c_void_p(h)
+
+    def _shape(self):
+        if self.layout == "interleaved":
+            return (self.batch,) + self.dims, torch.complex64
+        return (2, self.batch) + self.dims, torch.float32
+
+
 _cache: dict = {}
 _cache_lock = threading.Lock()
 
@@ -193,3 +223,33 @@ def fft(x: torch.Tensor, layout: str = "interleaved", precision: str = "fp32", o
 def ifft(x: torch.Tensor, layout: str = "interleaved", precision: str = "fp32", out=None) -> torch.Tensor:
     """Inverse transform of every row (exponent sign +1, unnormalised: ifft(fft(x)) = n x)."""
     return _run(x, True, layout, precision, out)
+
+
+_nd_cache: dict = {}
+
+
+def _run_nd(x: torch.Tensor, rank: int, inverse: bool, layout: str, out=None) -> torch.Tensor:
+    if layout == "interleaved":
+        if x.dtype != torch.complex64 or x.dim() != rank + 1:
+            raise ValueError(f"interleaved input must be a complex64 [batch, {rank} dims] tensor")
+        batch, dims = x.shape[0], tuple(x.shape[1:])
+    else:
+        if x.dtype != torch.float32 or x.dim() != rank + 2 or x.shape[0] != 2:
+            raise ValueError(f"split input must be a float32 [2, batch, {rank} dims] tensor")
+        batch, dims = x.shape[1], tuple(x.shape[2:])
+    key = (dims, batch, layout, inverse, x.device.index)
+    with _cache_lock:
+        p = _nd_cache.get(key)
+        if p is None:
+            p = _nd_cache[key] = NdPlan(dims, batch, layout, inverse, device=x.device)
+    return p.execute(x.contiguous(), out)
+
+
+def fftn(x: torch.Tensor, rank: int = 2, layout: str = "interleaved", out=None) -> torch.Tensor:
+    """Forward transform over the last `rank` (2 or 3) axes of every array in the batch."""
+    return _run_nd(x, rank, False, layout, out)
+
+
+def ifftn(x: torch.Tensor, rank: int = 2, layout: str = "interleaved", out=None) -> torch.Tensor:
+    """Inverse (unnormalised) transform over the last `rank` axes of every array in the batch."""
+    return _run_nd(x, rank, True, layout, out)

@@ -251,8 +251,9 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
         *passes = plan->npasses;
     }
     if (plan->mixed) cnt = mixed_radix_list(plan, tmp, 32);
+    if (plan->nd) cnt = 0;  // several 1D factorisations: the pass count alone is reported
     const int nsched = plan->fs ? 2 : plan->npasses;
-    for (int i = 0; i < nsched && !plan->uneven && !plan->mixed; ++i) {
+    for (int i = 0; i < nsched && !plan->uneven && !plan->mixed && !plan->nd; ++i) {
         const PassPlan &pp = plan->pass[i];
         HostSched h = host_sched(pp.logl, pp.loge, plan->precision != FFTC_FP32);
         for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];
@@ -270,6 +271,40 @@ fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream
     if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
         return FFTC_ERR_MISALIGNED;
     return plan_run(plan, in, out, nullptr, 0.f, (cudaStream_t)stream);
+}
+
+fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc_layout layout,
+                              fftc_direction direction, fftc_precision precision) {
+    if (rank < 2 || rank > 3 || !dims || batch < 0) return fail(FFTC_ERR_INVALID_VALUE);
+    if (layout != FFTC_LAYOUT_INTERLEAVED && layout != FFTC_LAYOUT_SPLIT) return fail(FFTC_ERR_INVALID_VALUE);
+    if (direction != FFTC_FORWARD && direction != FFTC_INVERSE) return fail(FFTC_ERR_INVALID_VALUE);
+    if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_BF16_TC_SPLIT)
+        return fail(FFTC_ERR_INVALID_VALUE);
+    if (precision != FFTC_FP32) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    int64_t per = 1;
+    for (int a = 0; a < rank; ++a) {
+        const int64_t d = dims[a];
+        const bool ok = a == rank - 1 ? (d >= 2 && d <= (int64_t(1) << 20) && (is_pow2(d) || mixed_supported(d)))
+                                      : nd_axis_supported(d);
+        if (!ok) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+        per *= d;
+        if (per > (int64_t(1) << 30)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    }
+    if (batch > (int64_t(1) << 30) / per) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    fftc_plan_s *p = new (std::nothrow) fftc_plan_s();
+    if (!p) return fail(FFTC_ERR_ALLOC);
+    p->magic = FFTC_PLAN_MAGIC;
+    p->n = per;
+    p->batch = batch;
+    p->layout = layout;
+    p->direction = direction;
+    p->precision = precision;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(FFTC_ERR_CUDA, p);
+    fftc_status st = nd_build(p, rank, dims);
+    if (st != FFTC_OK) return fail(st, p);
+    register_plan(p);
+    g_last_error = FFTC_OK;
+    return p;
 }
 
 fftc_plan fftc_plan_create_uneven(int64_t count, const int64_t *n, const int8_t *direction, const int64_t *offset,

@@ -156,16 +156,26 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
         mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_ROWS, LAYOUT_IL, LAYOUT_IL>(nt)
                                      : mixed_kernel<KIND_ROWS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt);
     else if (kind == KIND_COLS)
-        mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_COLS, LAYOUT_IL, LAYOUT_IL>(nt)
-                                     : mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL>(nt);
+        mp.kernel = lin == LAYOUT_IL       ? mixed_kernel<KIND_COLS, LAYOUT_IL, LAYOUT_IL>(nt)
+                    : lout == LAYOUT_SPLIT ? mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt)
+                                           : mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL>(nt);
     else
         mp.kernel = lout == LAYOUT_IL ? mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_IL>(nt)
                                       : mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT>(nt);
     mp.smem = (((C * a.pitch + 1) & ~1) + C * a.pitch) * (int)sizeof(float2);
-    if (mp.smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void *)mp.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mp.smem) !=
+    if (mp.smem > 48 * 1024) {
+        // the dynamic shared memory of one kernel differs from plan to plan: allow the
+        // device's maximum once (a smaller limit set for a later plan would break an
+        // earlier one); the launch's own size still sets the occupancy
+        int dev = 0, cap = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return FFTC_ERR_CUDA;
+        if (mp.smem > cap) return FFTC_ERR_UNSUPPORTED_SIZE;
+        if (cudaFuncSetAttribute((const void *)mp.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) !=
             cudaSuccess)
-        return FFTC_ERR_CUDA;
+            return FFTC_ERR_CUDA;
+    }
     mp.blocks = (a.p.total_lines + C - 1) / C;
     return FFTC_OK;
 }
@@ -281,6 +291,98 @@ fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st
     b.p.out = (float *)out;
     b.p.conj_out = inv;
     return mixed_launch(ms->pass[1], b, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Multidimensional transforms over [batch][d0]...[d_{r-1}] (rank 2 or 3): the DFT along
+// the contiguous last axis by a one-dimensional plan, then along every other axis a is a
+// strided pass of the column kind in place: line = (outer index, position l inside the
+// block of the later axes S = d_{a+1} ... d_{r-1}), element stride S, no inter-pass twiddle.
+// This is the (F (x) I)(I (x) F) form of Section 3 with both factors whole transforms.
+// ---------------------------------------------------------------------------
+
+struct NdState {
+    fftc_plan_s *rows = nullptr;
+    int naxes = 0;
+    MixedPass axes[2];
+};
+
+bool nd_axis_supported(int64_t d) { return d >= 2 && d <= kMixedSinglePass && mixed_supported(d); }
+
+fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
+    NdState *nd = new (std::nothrow) NdState();
+    if (!nd) return FFTC_ERR_ALLOC;
+    p->nd = nd;
+    const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
+    int64_t total = p->batch;
+    for (int a = 0; a < rank; ++a) total *= dims[a];
+    p->total_elems = total;
+    void *d = nullptr;
+    if (plan_alloc(p, 16, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->d_err = (int *)d;
+    if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
+    // the last axis: a one-dimensional plan over batch * d0 ... d_{r-2} contiguous rows
+    fftc_plan_s *r = new (std::nothrow) fftc_plan_s();
+    if (!r) return FFTC_ERR_ALLOC;
+    nd->rows = r;
+    r->magic = p->magic;
+    r->device = p->device;
+    r->n = dims[rank - 1];
+    r->logn = 0;
+    while ((int64_t(1) << (r->logn + 1)) <= r->n) ++r->logn;
+    r->batch = total / r->n;
+    r->layout = p->layout;
+    r->direction = p->direction;
+    r->precision = p->precision;
+    fftc_status st = plan_build(r);
+    if (st != FFTC_OK) return st;
+    const int64_t plane = lay == LAYOUT_SPLIT ? total : 0;
+    for (int a = rank - 2; a >= 0; --a) {
+        int64_t S = 1, outer = p->batch;
+        for (int b = a + 1; b < rank; ++b) S *= dims[b];
+        for (int b = 0; b < a; ++b) outer *= dims[b];
+        const int64_t L = dims[a];
+        MixedPass &mp = nd->axes[nd->naxes++];
+        PassParams &b = mp.args.p;
+        memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
+        b.in_plane = b.out_plane = plane;
+        b.total_lines = outer * S;
+        b.in_tr = b.out_tr = L * S;
+        b.in_line = b.out_line = 1;
+        b.in_elem = b.out_elem = S;
+        if (b.total_lines + mixed_lines(L) >= (int64_t(1) << 31)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        st = mixed_pass_setup(p, mp, L, (int)std::min<int64_t>(S, mixed_lines(L)), KIND_COLS, lay, lay, S);
+        if (st != FFTC_OK) return st;
+    }
+    p->npasses = r->npasses + nd->naxes;
+    return FFTC_OK;
+}
+
+fftc_status nd_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st) {
+    NdState *nd = p->nd;
+    fftc_status s = plan_run(nd->rows, in, out, nullptr, 0.f, st);
+    if (s != FFTC_OK) return s;
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    for (int i = 0; i < nd->naxes; ++i) {  // in place: a tile is read whole before it is written
+        MixedArgs a = nd->axes[i].args;
+        a.p.in = (const float *)out;
+        a.p.out = (float *)out;
+        a.p.conj_in = a.p.conj_out = inv;
+        if (mixed_launch(nd->axes[i], a, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    }
+    return FFTC_OK;
+}
+
+void nd_free(fftc_plan_s *p) {
+    if (!p->nd) return;
+    if (p->nd->rows) {
+        plan_destroy_extra(p->nd->rows);
+        plan_free_device(p->nd->rows);
+        delete p->nd->rows;
+    }
+    delete p->nd;
+    p->nd = nullptr;
 }
 
 int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap) {

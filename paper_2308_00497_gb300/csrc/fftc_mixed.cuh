@@ -357,12 +357,13 @@ __device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, cons
         const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
         float2 x = sm[c * a.pitch + e];
         if constexpr (KIND == KIND_COLS) {
-            // inter-pass diagonal of Eq. 1: column l, output row e: w_N^(l e)
-            x = cmul(x, __ldg(p.tw2_full + (int64_t)e * a.lpt + l));
+            // inter-pass diagonal of Eq. 1: column l, output row e: w_N^(l e) (four-step only;
+            // a strided axis of a multidimensional transform has none)
+            if (p.tw2_full) x = cmul(x, __ldg(p.tw2_full + (int64_t)e * a.lpt + l));
         }
         if (cj) x.y = -x.y;
         const int64_t off = tr * p.out_tr + l * p.out_line + (int64_t)e * p.out_elem;
-        if constexpr (KIND == KIND_COLS) {
+        if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
             __stcg(reinterpret_cast<float2 *>(p.out) + off, x);  // workspace: keep it in L2
         } else if constexpr (LOUT == LAYOUT_IL) {
             __stcs(reinterpret_cast<float2 *>(p.out) + off, x);

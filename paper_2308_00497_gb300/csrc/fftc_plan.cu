@@ -334,10 +334,10 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     }
     if (p->precision != FFTC_FP32 && post_h) return FFTC_ERR_INVALID_VALUE;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
-    if (p->mixed) {
+    if (p->mixed || p->nd) {
         if (post_h) return FFTC_ERR_INVALID_VALUE;
         if (ev) cudaEventRecord(ev[0], st);
-        fftc_status s = mixed_run(p, in, out, st);
+        fftc_status s = p->nd ? nd_run(p, in, out, st) : mixed_run(p, in, out, st);
         if (ev) {
             cudaEventRecord(ev[1], st);
             cudaEventRecord(ev[2], st);
@@ -381,7 +381,7 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
 }
 
 fftc_status plan_run_range(fftc_plan_s *p, const void *in, void *out, int64_t b0, int64_t nb, cudaStream_t st) {
-    if (p->uneven || p->fs || p->mixed || p->precision != FFTC_FP32 || b0 < 0 || nb < 0 || b0 + nb > p->batch)
+    if (p->uneven || p->fs || p->mixed || p->nd || p->precision != FFTC_FP32 || b0 < 0 || nb < 0 || b0 + nb > p->batch)
         return FFTC_ERR_INVALID_VALUE;
     if (nb == 0) return FFTC_OK;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
@@ -417,6 +417,7 @@ void plan_destroy_extra(fftc_plan_s *p) {
     uneven_free(p);
     fs_free(p);
     mixed_free(p);
+    nd_free(p);
     host_free(p);
 }
 

@@ -24,6 +24,7 @@ struct UnevenState;  // persistent uneven-batch executor (fftc_uneven.cu)
 struct FsState;      // L2-resident four-step executor (fftc_fourstep_l2.cu)
 struct TcState;      // tensor-core radix-16 executor (fftc_tc.cu)
 struct MixedState;   // mixed-radix passes (fftc_mixed.cu)
+struct NdState;      // multidimensional transforms (fftc_mixed.cu)
 
 }  // namespace fftc
 
@@ -47,6 +48,7 @@ struct fftc_plan_s {
     fftc::TcState *tc = nullptr;
     fftc::FsState *fs = nullptr;
     fftc::MixedState *mixed = nullptr;  // n with factors 3, 5 or 7 (fftc_mixed.cu)
+    fftc::NdState *nd = nullptr;        // rank 2 / 3 transforms (fftc_mixed.cu)
     std::vector<void *> dev_allocs;
     // timing probe: events[slot * 3 + i] before pass i (i < npasses) and after the last
     std::vector<cudaEvent_t> probe_events;
@@ -92,6 +94,12 @@ fftc_status mixed_build(fftc_plan_s *p);
 fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
 int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap);
 void mixed_free(fftc_plan_s *p);
+
+// multidimensional transforms: a 1D plan along the last axis, strided passes along the others
+bool nd_axis_supported(int64_t d);
+fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims);
+fftc_status nd_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
+void nd_free(fftc_plan_s *p);
 
 // L2-resident four-step (fftc_fourstep_l2.cu)
 bool fs_available(int logn, int lay);

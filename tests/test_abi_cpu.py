@@ -97,3 +97,24 @@ def test_uneven_validation_before_any_device_call(lib):
     assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE
     assert not lib.fftc_plan_create_uneven(1, n.ctypes.data, d.ctypes.data, o.ctypes.data, 1, 0)
     assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE          # split layout
+
+
+@pytest.mark.parametrize("dims", [(16384, 4), (11, 16), (4, 22), (1, 8), (8, 1 << 21)])
+def test_nd_unsupported_shapes_rejected_before_any_device_call(lib, dims):
+    import ctypes
+    from paper_2308_00497_gb300 import _native as nat
+    arr = (ctypes.c_int64 * len(dims))(*dims)
+    assert not lib.fftc_plan_create_nd(len(dims), arr, 2, 0, -1, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
+
+
+def test_nd_bad_arguments_rejected(lib):
+    import ctypes
+    from paper_2308_00497_gb300 import _native as nat
+    arr = (ctypes.c_int64 * 4)(8, 8, 8, 8)
+    for args in ((1, arr, 2, 0, -1, 0), (4, arr, 2, 0, -1, 0), (2, None, 2, 0, -1, 0), (2, arr, -1, 0, -1, 0),
+                 (2, arr, 2, 5, -1, 0), (2, arr, 2, 0, 3, 0)):
+        assert not lib.fftc_plan_create_nd(*args)
+        assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE
+    assert not lib.fftc_plan_create_nd(2, arr, 2, 0, -1, 1)  # tensor-core precisions: 1D only
+    assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
