@@ -427,9 +427,34 @@ def run_extras(args, dev) -> dict:
                               "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
     del xs, ts, xf
     out["mixed_radix"] = run_mixed(dev, reps)
+    out["multidim"] = run_nd(dev, reps)
     if not args.no_precision:
         out["precision"] = run_precision(args, dev, reps)
     return out
+
+
+ND_SHAPES = [(1024, 1024), (4096, 4096), (1000, 1000), (256, 256, 256), (64, 64, 64)]
+
+
+def run_nd(dev, reps: int) -> dict:
+    """Rank-2/3 arrays, batch = 2^26 // elements, forward, interleaved: ms, GFLOP/s
+    (5 N log2 N per array), HBM passes and the strict HBM fraction (16 B per element)."""
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    res = []
+    for dims in ND_SHAPES:
+        N = int(math.prod(dims))
+        B = max(1, ELEMS // N)
+        x = torch.randn(B * N, dtype=torch.complex64, device=dev).view((B,) + dims)
+        y = torch.empty_like(x)
+        p = fc.NdPlan(dims, B, "interleaved", False, device=dev)
+        t = _time_ms(lambda: p.execute(x, y), reps)
+        res.append({"dims": list(dims), "batch": B, "passes": p.info()[0], "ms": round(t, 4),
+                    "gflops": round(5.0 * N * math.log2(N) * B / (t * 1e-3) / 1e9, 1),
+                    "hbm_frac_strict": round(16.0 * N * B / (t * 1e-3) / 1e9 / peaks()[0], 4)})
+        del x, y, p
+    return {"workload": "rank-2/3 C2C, batch * elements ~ 2^26, forward, interleaved", "results": res}
 
 
 MIXED_SIZES = [12, 96, 360, 1000, 3072, 6000, 10000, 59049, 100000, 1000000]

@@ -305,7 +305,23 @@ struct NdState {
     fftc_plan_s *rows = nullptr;
     int naxes = 0;
     MixedPass axes[2];
+    // interleaved power-of-two axes of 64..1024 points: the compiled column pass
+    // (k_pass, runtime element stride) instead of the runtime-radix kernel
+    const KernelEntry *fast[2] = {nullptr, nullptr};
+    PassParams fastp[2];
 };
+
+// compiled column-pass shape for a strided power-of-two axis (log2 length, log2 elements
+// per thread, columns per tile), or false
+static bool nd_fast_shape(int64_t L, int *logl, int *loge, int *lines) {
+    if (L < 64 || L > 1024 || (L & (L - 1)) != 0) return false;
+    int l = 0;
+    while ((int64_t(1) << l) < L) ++l;
+    *logl = l;
+    *loge = l == 10 ? 5 : 4;
+    *lines = l == 10 ? 8 : 16;
+    return true;
+}
 
 bool nd_axis_supported(int64_t d) { return d >= 2 && d <= kMixedSinglePass && mixed_supported(d); }
 
@@ -342,7 +358,35 @@ fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
         for (int b = a + 1; b < rank; ++b) S *= dims[b];
         for (int b = 0; b < a; ++b) outer *= dims[b];
         const int64_t L = dims[a];
-        MixedPass &mp = nd->axes[nd->naxes++];
+        const int ax = nd->naxes++;
+        int logl = 0, loge = 0, lines = 0;
+        if (lay == LAYOUT_IL && (S & (S - 1)) == 0 && nd_fast_shape(L, &logl, &loge, &lines)) {
+            const KernelEntry *k = find_kernel(KIND_COLS, logl, loge, lines, LAYOUT_IL, LAYOUT_IL, 0, 0);
+            if (k) {
+                PassParams &q = nd->fastp[ax];
+                memset(&q, 0, sizeof(q));
+                q.err = p->d_err;
+                q.total_lines = outer * S;
+                int ls = 0;
+                while ((int64_t(1) << ls) < S) ++ls;
+                q.log_lpt = ls;
+                q.in_tr = q.out_tr = L * S;
+                q.in_line = q.out_line = 1;
+                q.in_elem = q.out_elem = S;
+                // prefetch the next wave's column bands into L2 (tiles inside one block only)
+                q.pf_tiles = S >= lines ? -1 : 0;
+                std::vector<float2> tw;
+                stage_twiddles(logl, loge, tw);
+                if (!tw.empty()) {
+                    if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+                    q.tw = (const float2 *)d;
+                }
+                if (k->prepare() != cudaSuccess) return FFTC_ERR_CUDA;
+                nd->fast[ax] = k;
+                continue;
+            }
+        }
+        MixedPass &mp = nd->axes[ax];
         PassParams &b = mp.args.p;
         memset(&b, 0, sizeof(b));
         b.err = p->d_err;
@@ -365,6 +409,14 @@ fftc_status nd_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st) {
     if (s != FFTC_OK) return s;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
     for (int i = 0; i < nd->naxes; ++i) {  // in place: a tile is read whole before it is written
+        if (nd->fast[i]) {
+            PassParams q = nd->fastp[i];
+            q.in = (const float *)out;
+            q.out = (float *)out;
+            q.conj_in = q.conj_out = inv;
+            if (nd->fast[i]->launch(q, st) != cudaSuccess) return FFTC_ERR_CUDA;
+            continue;
+        }
         MixedArgs a = nd->axes[i].args;
         a.p.in = (const float *)out;
         a.p.out = (float *)out;

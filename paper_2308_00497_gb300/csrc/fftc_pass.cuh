@@ -151,7 +151,7 @@ struct Pass {
                     // inter-pass twiddle of Eq. 1 applied at the memory level: w_N^(b t')
                     if (dtab) {
                         x = cmul(x, __ldg(dtab + a0 * es + off));
-                    } else {
+                    } else if (p.tw2_lo) {  // none for a strided axis of a multidimensional array
                         const int a = a0 + t * (L / R);
                         const int m = (l * a) & ((1 << p.log_n2) - 1);
                         x = cmul(x, cmul(__ldg(p.tw2_lo + (m & ((1 << p.tw2_lo_bits) - 1))),
