@@ -235,7 +235,10 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
         B = ELEMS // n
         for layout in args.layouts:
             for inv in args.dirs:
-                plans.append((e, layout, inv, fc.Plan(n, B, layout, inv, device=dev)))
+                pl = fc.Plan(n, B, layout, inv, device=dev)
+                if args.tune:
+                    pl.tune(3)  # measure-mode planning, outside the timed region
+                plans.append((e, layout, inv, pl))
 
     def views(layout, n, B):
         if layout == "interleaved":
@@ -340,6 +343,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
             "config": {"workload": WORKLOAD, "n": "2^8..2^20", "n_times_batch": ELEMS,
                        "layouts": LAYOUTS, "directions": ["forward", "inverse"],
                        "l2": "no flush: every buffer is 512 MiB, larger than L2",
+                       "planning": "measure (fftc_plan_tune, untimed)" if args.tune else "default table",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -536,6 +540,8 @@ def main():
                     help="log2 n list (default: the whole sweep); a subset is for profiling only")
     ap.add_argument("--layouts", default=",".join(LAYOUTS))
     ap.add_argument("--dirs", default="fwd,inv")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="1: measure-mode planning (fftc_plan_tune) before timing; 0: the default table")
     args = ap.parse_args()
     args.sizes = [int(v) for v in args.sizes.split(",")]
     args.layouts = args.layouts.split(",")

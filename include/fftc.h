@@ -136,6 +136,21 @@ const char *fftc_status_string(fftc_status s);
 fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices);
 
 /*
+ * Measure-mode planning (the runtime search over decompositions that the paper leaves
+ * to future work, Section 6; FFTW's "measure"): times, on scratch device buffers of the
+ * plan's size allocated and freed inside the call, `reps` launches of every compiled
+ * kernel that can run each pass of this plan (single pass: every rows kernel for its n
+ * and layout, with each landing-buffer and refill variant, elements per thread and tile
+ * height; four-step: every column kernel for pass 1, with and without the L2 prefetch,
+ * and every transposed-row kernel for pass 2, for the plan's split n = M*K), and keeps
+ * the fastest. Choices are cached per (n, batch, layout, direction) for the process, so a
+ * second plan of the same shape is tuned without timing. Synchronises the device; do not
+ * call it while the plan executes. Mixed-radix, multidimensional, uneven and tensor-core
+ * plans are returned unchanged. reps in [1, 1000].
+ */
+fftc_status fftc_plan_tune(fftc_plan plan, int reps);
+
+/*
  * Multidimensional transforms: `batch` arrays of rank 2 or 3, dims[0] x ... x dims[rank-1]
  * stored row-major (the last axis contiguous), array b at element offset b * prod(dims);
  * the split layout keeps one real plane and one imaginary plane for the whole batch.

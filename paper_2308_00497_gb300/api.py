@@ -95,6 +95,13 @@ class Plan:
                                                dev_buf.data_ptr(), _stream_handle(stream)), "fftc_execute_host")
         return host_out
 
+    def tune(self, reps: int = 5):
+        """Time every compiled kernel that can run this plan's passes; keep the fastest
+        (fftc_plan_tune, cached per shape for the process)."""
+        with torch.cuda.device(self.device):
+            nat.check(nat.load().fftc_plan_tune(self._h, int(reps)), "fftc_plan_tune")
+        return self
+
     def timing(self, enable: bool):
         """Start (or stop and drop) the per-pass event probe (fftc_plan_timing)."""
         nat.check(nat.load().fftc_plan_timing(self._h, 1 if enable else 0), "fftc_plan_timing")

@@ -273,6 +273,12 @@ fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream
     return plan_run(plan, in, out, nullptr, 0.f, (cudaStream_t)stream);
 }
 
+fftc_status fftc_plan_tune(fftc_plan plan, int reps) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    if (reps < 1 || reps > 1000) return FFTC_ERR_INVALID_VALUE;
+    return plan_tune(plan, reps);
+}
+
 fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc_layout layout,
                               fftc_direction direction, fftc_precision precision) {
     if (rank < 2 || rank > 3 || !dims || batch < 0) return fail(FFTC_ERR_INVALID_VALUE);

@@ -95,6 +95,10 @@ fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st
 int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap);
 void mixed_free(fftc_plan_s *p);
 
+// time every compiled kernel that can run each pass of the plan and keep the fastest
+// (fftc_tune.cu)
+fftc_status plan_tune(fftc_plan_s *p, int reps);
+
 // multidimensional transforms: a 1D plan along the last axis, strided passes along the others
 bool nd_axis_supported(int64_t d);
 fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims);

@@ -1,0 +1,191 @@
+// Measurement-driven kernel choice for a plan (FFTW's "measure" planning, the runtime
+// decomposition search the paper leaves to future work, Section 6): every compiled kernel
+// that can run a pass of this plan is timed on scratch buffers of the plan's size and the
+// fastest is kept.
+//   single pass: every registered rows kernel for (n, layout): plain, bulk-copy fed with
+//                each landing-buffer count and refill point, each elements-per-thread
+//                and tile height;
+//   four-step:   for the plan's split n = M K, every column kernel for pass 1 (plain with
+//                and without the L2 prefetch, tensor-map fed; compile-time or runtime
+//                stride) and every transposed-row kernel for pass 2, timed pass by pass.
+// Choices are cached per (n, batch, layout, direction) for the process.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "fftc_plan.h"
+
+namespace fftc {
+
+namespace {
+
+struct Choice {
+    const KernelEntry *k1 = nullptr, *k2 = nullptr;
+    int pf1 = 0;
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int, int>, Choice> g_tune_cache;
+
+struct Scratch {
+    void *in = nullptr, *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Scratch() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (st) cudaStreamDestroy(st);
+        if (in) cudaFree(in);
+        if (out) cudaFree(out);
+    }
+};
+
+// stage tables of (logl, loge), uploaded once per plan (NULL for a single-stage line,
+// which reads none); false if the upload failed
+bool tables_for(fftc_plan_s *p, std::map<std::pair<int, int>, const float2 *> &cache, int logl, int loge,
+                const float2 **out) {
+    auto it = cache.find({logl, loge});
+    if (it != cache.end()) {
+        *out = it->second;
+        return true;
+    }
+    std::vector<float2> tw;
+    stage_twiddles(logl, loge, tw);
+    void *d = nullptr;
+    if (!tw.empty() && plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return false;
+    cache[{logl, loge}] = (const float2 *)d;
+    *out = (const float2 *)d;
+    return true;
+}
+
+// mean milliseconds of one launch of `k` with `a`, or a negative value if it cannot run
+float time_launch(const KernelEntry *k, const PassParams &a, Scratch &s, int reps) {
+    if (k->prepare() != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    if (k->launch(a, s.st) != cudaSuccess || cudaStreamSynchronize(s.st) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    cudaEventRecord(s.a, s.st);
+    for (int i = 0; i < reps; ++i) k->launch(a, s.st);
+    cudaEventRecord(s.b, s.st);
+    if (cudaEventSynchronize(s.b) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s.a, s.b);
+    return ms / reps;
+}
+
+fftc_status apply(fftc_plan_s *p, const Choice &c, std::map<std::pair<int, int>, const float2 *> &tabs) {
+    const float2 *t0 = nullptr, *t1 = nullptr;
+    if (!tables_for(p, tabs, c.k1->logl, c.k1->loge, &t0)) return FFTC_ERR_ALLOC;
+    if (p->npasses == 2 && !tables_for(p, tabs, c.k2->logl, c.k2->loge, &t1)) return FFTC_ERR_ALLOC;
+    if (c.k1->prepare() != cudaSuccess || (p->npasses == 2 && c.k2->prepare() != cudaSuccess)) return FFTC_ERR_CUDA;
+    PassPlan &p0 = p->pass[0];
+    p0.k = c.k1;
+    p0.loge = c.k1->loge;
+    p0.lines = c.k1->lines;
+    p0.tw = const_cast<float2 *>(t0);
+    p0.base.tw = t0;
+    if (p->npasses == 2) {
+        p0.base.pf_tiles = c.pf1;
+        PassPlan &p1 = p->pass[1];
+        p1.k = c.k2;
+        p1.loge = c.k2->loge;
+        p1.lines = c.k2->lines;
+        p1.tw = const_cast<float2 *>(t1);
+        p1.base.tw = t1;
+    }
+    return FFTC_OK;
+}
+
+}  // namespace
+
+fftc_status plan_tune(fftc_plan_s *p, int reps) {
+    if (p->uneven || p->fs || p->mixed || p->nd || p->precision != FFTC_FP32 || p->batch == 0) return FFTC_OK;
+    if (reps < 1) reps = 1;
+    const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
+    const auto key = std::make_tuple(p->n, p->batch, (int)p->layout, (int)p->direction);
+    std::map<std::pair<int, int>, const float2 *> tabs;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return apply(p, it->second, tabs);
+    }
+    Scratch s;
+    const size_t bytes = (size_t)p->total_elems * 8;
+    if (cudaMalloc(&s.in, bytes) != cudaSuccess || cudaMalloc(&s.out, bytes) != cudaSuccess) return FFTC_ERR_ALLOC;
+    if (cudaMemset(s.in, 0, bytes) != cudaSuccess || cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&s.a) != cudaSuccess || cudaEventCreate(&s.b) != cudaSuccess)
+        return FFTC_ERR_CUDA;
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    Choice best;
+    best.k1 = p->pass[0].k;
+    best.k2 = p->npasses == 2 ? p->pass[1].k : nullptr;
+    best.pf1 = p->pass[0].base.pf_tiles;
+    float t1 = 1e30f, t2 = 1e30f;
+    const PassPlan &p0 = p->pass[0];
+    for (int i = 0; i < kernel_count(); ++i) {
+        const KernelEntry *e = kernel_at(i);
+        if (e->prec != 0) continue;
+        if (p->npasses == 1) {
+            if (e->kind != KIND_ROWS || e->logl != p0.logl || e->lin != lay || e->lout != lay) continue;
+            PassParams a = p0.base;
+            if (!tables_for(p, tabs, e->logl, e->loge, &a.tw)) return FFTC_ERR_ALLOC;
+            a.in = (const float *)s.in;
+            a.out = (float *)s.out;
+            a.conj_in = a.conj_out = inv;
+            const float t = time_launch(e, a, s, reps);
+            if (t > 0.f && t < t1) {
+                t1 = t;
+                best.k1 = e;
+            }
+            continue;
+        }
+        const PassPlan &p1 = p->pass[1];
+        if (e->kind == KIND_COLS && e->logl == p0.logl && e->lin == lay && e->lout == LAYOUT_IL &&
+            (e->logx == 0 || e->logx == p1.logl)) {
+            for (int pf : {0, -1}) {
+                if (pf && e->pipe) continue;  // the prefetch belongs to the plain kernel
+                PassParams a = p0.base;
+                if (!tables_for(p, tabs, e->logl, e->loge, &a.tw)) return FFTC_ERR_ALLOC;
+                a.pf_tiles = pf;
+                a.in = (const float *)s.in;
+                a.out = (float *)p->workspace;
+                a.conj_in = inv;
+                a.conj_out = 0;
+                const float t = time_launch(e, a, s, reps);
+                if (t > 0.f && t < t1) {
+                    t1 = t;
+                    best.k1 = e;
+                    best.pf1 = pf;
+                }
+            }
+        } else if (e->kind == KIND_ROWST && e->logl == p1.logl && e->lin == LAYOUT_IL && e->lout == lay &&
+                   (e->logx == 0 || e->logx == p0.logl)) {
+            PassParams b = p1.base;
+            if (!tables_for(p, tabs, e->logl, e->loge, &b.tw)) return FFTC_ERR_ALLOC;
+            b.in = (const float *)p->workspace;
+            b.out = (float *)s.out;
+            b.conj_in = 0;
+            b.conj_out = inv;
+            const float t = time_launch(e, b, s, reps);
+            if (t > 0.f && t < t2) {
+                t2 = t;
+                best.k2 = e;
+            }
+        }
+    }
+    if (!best.k1 || (p->npasses == 2 && !best.k2)) return FFTC_ERR_UNSUPPORTED_SIZE;
+    const fftc_status st = apply(p, best, tabs);
+    if (st != FFTC_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return FFTC_OK;
+}
+
+}  // namespace fftc

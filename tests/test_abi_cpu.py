@@ -118,3 +118,8 @@ def test_nd_bad_arguments_rejected(lib):
         assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE
     assert not lib.fftc_plan_create_nd(2, arr, 2, 0, -1, 1)  # tensor-core precisions: 1D only
     assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
+
+
+def test_tune_rejects_null_plan_and_bad_reps(lib):
+    from paper_2308_00497_gb300 import _native as nat
+    assert lib.fftc_plan_tune(None, 3) == nat.ERR_INVALID_PLAN

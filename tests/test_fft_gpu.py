@@ -253,3 +253,23 @@ def test_execute_host_chunked_matches_device_path(e, B, layout, inverse):
     y = from_device(out.cuda(), layout)
     ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
     assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [6, 10, 13, 14, 15, 18, 20])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_tuned_plan_matches_oracle(e, layout):
+    """fftc_plan_tune swaps in the fastest compiled kernels; results stay within tolerance,
+    and a second plan of the same shape reuses the cached choice."""
+    import paper_2308_00497_gb300 as fc
+    n = 1 << e
+    B = max(3, (1 << 22) // n)
+    x = si.uniform_complex(B, n, seed=e + 40)
+    inverse = e % 2 == 1
+    for _ in range(2):
+        p = fc.Plan(n, B, layout, inverse).tune(3)
+        y = from_device(p.execute(to_device(x, layout)), layout)
+        torch.cuda.synchronize()
+        p.check()
+        rows = np.array([0, B // 2, B - 1])
+        ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
+        assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
