@@ -49,13 +49,17 @@ typedef enum { FFTC_FORWARD = -1, FFTC_INVERSE = +1 } fftc_direction;
  *                 tensor cores with FP16 or BF16 operands and FP32 accumulation.
  * *_TC_SPLIT:     as *_TC, but each operand is split into hi + lo parts and the three
  *                 products hi*hi + hi*lo + lo*hi are accumulated, recovering most of
- *                 the FP32 accuracy. */
+ *                 the FP32 accuracy.
+ * FP64:           complex128 data, every stage in float64 (the runtime-radix kernel,
+ *                 any supported n). */
 typedef enum {
     FFTC_FP32 = 0,
     FFTC_FP16_TC = 1,
     FFTC_BF16_TC = 2,
     FFTC_FP16_TC_SPLIT = 3,
-    FFTC_BF16_TC_SPLIT = 4
+    FFTC_BF16_TC_SPLIT = 4,
+    FFTC_FP64 = 5 /* complex128 data ([batch][n] double pairs, or two double planes) and
+                     FP64 arithmetic and tables: the paper's own precision (Section 4) */
 } fftc_precision;
 
 typedef enum {
@@ -80,7 +84,8 @@ typedef enum {
  * Precomputes the twiddle diagonals D (Eq. 1; Table 1 "Mul") in FP64 with exact
  * integer angle reduction and rounds them once to the working precision.
  * Returns NULL on error; fftc_get_last_error() then tells why.
- * Tensor-core precisions require a power of two n >= 16.
+ * Tensor-core precisions require a power of two n >= 16. FFTC_FP64 takes any n the
+ * FP32 path takes (one pass up to 4096, two above); its buffers hold complex128.
  */
 fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_direction direction,
                            fftc_precision precision);
@@ -115,7 +120,8 @@ fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_ou
 fftc_status fftc_execute_pointwise(fftc_plan plan, const void *in, void *out, const float *h, float scale,
                                    void *stream);
 
-/* Bytes of one input (or output) buffer of the plan; 0 for an invalid plan. */
+/* Bytes of one input (or output) buffer of the plan (8 or, for FFTC_FP64, 16 per
+ * complex element); 0 for an invalid plan. */
 int64_t fftc_plan_bytes(fftc_plan plan);
 
 /* Release the plan and its device memory. NULL is a no-op returning FFTC_OK. */

@@ -14,13 +14,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfftc.so")
 # enums of include/fftc.h
 LAYOUT_INTERLEAVED, LAYOUT_SPLIT = 0, 1
 FORWARD, INVERSE = -1, 1
-FP32, FP16_TC, BF16_TC, FP16_TC_SPLIT, BF16_TC_SPLIT = 0, 1, 2, 3, 4
+FP32, FP16_TC, BF16_TC, FP16_TC_SPLIT, BF16_TC_SPLIT, FP64 = 0, 1, 2, 3, 4, 5
 (OK, ERR_INVALID_VALUE, ERR_UNSUPPORTED_SIZE, ERR_MISALIGNED, ERR_ALLOC, ERR_CUDA,
  ERR_INVALID_PLAN, ERR_TIMEOUT) = range(8)
 
 LAYOUTS = {"interleaved": LAYOUT_INTERLEAVED, "split": LAYOUT_SPLIT}
 PRECISIONS = {"fp32": FP32, "fp16_tc": FP16_TC, "bf16_tc": BF16_TC,
-              "fp16_tc_split": FP16_TC_SPLIT, "bf16_tc_split": BF16_TC_SPLIT}
+              "fp16_tc_split": FP16_TC_SPLIT, "bf16_tc_split": BF16_TC_SPLIT, "fp64": FP64}
 
 _c_i64, _c_int, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
 

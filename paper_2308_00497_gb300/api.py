@@ -51,9 +51,10 @@ class Plan:
         return p.value, [r[i] for i in range(min(c.value, 16))]
 
     def _shape(self):
+        fp64 = self.precision == "fp64"
         if self.layout == "interleaved":
-            return (self.batch, self.n), torch.complex64
-        return (2, self.batch, self.n), torch.float32
+            return (self.batch, self.n), torch.complex128 if fp64 else torch.complex64
+        return (2, self.batch, self.n), torch.float64 if fp64 else torch.float32
 
     def _check_tensor(self, t: torch.Tensor, name: str):
         shape, dtype = self._shape()
@@ -210,13 +211,17 @@ def get_plan(n: int, batch: int, layout: str = "interleaved", inverse: bool = Fa
 
 
 def _run(x: torch.Tensor, inverse: bool, layout: str, precision: str, out=None) -> torch.Tensor:
+    if x.dtype in (torch.complex128, torch.float64):
+        precision = "fp64"  # complex128 data: the FP64 path
+    want = {"interleaved": torch.complex128 if precision == "fp64" else torch.complex64,
+            "split": torch.float64 if precision == "fp64" else torch.float32}[layout]
     if layout == "interleaved":
-        if x.dtype != torch.complex64 or x.dim() != 2:
-            raise ValueError("interleaved input must be a complex64 [batch, n] tensor")
+        if x.dtype != want or x.dim() != 2:
+            raise ValueError(f"interleaved input must be a {want} [batch, n] tensor")
         batch, n = x.shape
     else:
-        if x.dtype != torch.float32 or x.dim() != 3 or x.shape[0] != 2:
-            raise ValueError("split input must be a float32 [2, batch, n] tensor")
+        if x.dtype != want or x.dim() != 3 or x.shape[0] != 2:
+            raise ValueError(f"split input must be a {want} [2, batch, n] tensor")
         batch, n = x.shape[1], x.shape[2]
     x = x.contiguous()
     return get_plan(n, batch, layout, inverse, precision, device=x.device).execute(x, out)

@@ -198,11 +198,11 @@ fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_di
                            fftc_precision precision) {
     if (layout != FFTC_LAYOUT_INTERLEAVED && layout != FFTC_LAYOUT_SPLIT) return fail(FFTC_ERR_INVALID_VALUE);
     if (direction != FFTC_FORWARD && direction != FFTC_INVERSE) return fail(FFTC_ERR_INVALID_VALUE);
-    if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_BF16_TC_SPLIT)
-        return fail(FFTC_ERR_INVALID_VALUE);
+    if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_FP64) return fail(FFTC_ERR_INVALID_VALUE);
     if (batch < 0) return fail(FFTC_ERR_INVALID_VALUE);
     if (n < 2 || n > (int64_t(1) << 20)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
-    if (!is_pow2(n) && (!mixed_supported(n) || precision != FFTC_FP32)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    const bool tc = precision != FFTC_FP32 && precision != FFTC_FP64;
+    if (!is_pow2(n) && (!mixed_supported(n) || tc)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
     if (batch > (int64_t(1) << 40) / n) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
 
     fftc_plan_s *p = new (std::nothrow) fftc_plan_s();
@@ -236,7 +236,7 @@ fftc_status fftc_destroy(fftc_plan plan) {
 
 int64_t fftc_plan_bytes(fftc_plan plan) {
     if (!is_live(plan)) return 0;
-    return plan->total_elems * 8;
+    return plan->total_elems * (plan->precision == FFTC_FP64 ? 16 : 8);
 }
 
 fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices) {
@@ -284,8 +284,7 @@ fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc
     if (rank < 2 || rank > 3 || !dims || batch < 0) return fail(FFTC_ERR_INVALID_VALUE);
     if (layout != FFTC_LAYOUT_INTERLEAVED && layout != FFTC_LAYOUT_SPLIT) return fail(FFTC_ERR_INVALID_VALUE);
     if (direction != FFTC_FORWARD && direction != FFTC_INVERSE) return fail(FFTC_ERR_INVALID_VALUE);
-    if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_BF16_TC_SPLIT)
-        return fail(FFTC_ERR_INVALID_VALUE);
+    if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_FP64) return fail(FFTC_ERR_INVALID_VALUE);
     if (precision != FFTC_FP32) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
     int64_t per = 1;
     for (int a = 0; a < rank; ++a) {

@@ -65,7 +65,7 @@ fftc_status host_execute(fftc_plan_s *p, const void *host_in, void *host_out, vo
     int64_t cb = std::max<int64_t>(1, kChunkBytes / (n * 8));
     cb = (cb + 3) / 4 * 4;
     const bool chunked = !p->uneven && !p->fs && !p->mixed && !p->nd && p->precision == FFTC_FP32 && B > cb;
-    const size_t bytes = (size_t)p->total_elems * 8;
+    const size_t bytes = (size_t)p->total_elems * (p->precision == FFTC_FP64 ? 16 : 8);
     if (!chunked) {
         if (cudaMemcpyAsync(dev_buf, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FFTC_ERR_CUDA;
         fftc_status s = plan_run(p, dev_buf, dev_buf, nullptr, 0.f, st);

@@ -15,8 +15,10 @@
 
 namespace fftc {
 
-static const int kMixedSinglePass = 8192;  // longest line one CTA transforms (2 x 64 KB)
-static const int kMixedTile = 4096;        // elements per CTA tile for shorter lines
+static const int kMixedSinglePass = 8192;  // longest FP32 line one CTA transforms (2 x 64 KB)
+static const int kMixedTile = 4096;        // FP32 elements per CTA tile for shorter lines
+static const int kMixedSinglePass64 = 4096;  // the same for FP64 (16-byte elements)
+static const int kMixedTile64 = 2048;
 
 typedef void (*MixedKernel)(MixedArgs);
 
@@ -26,6 +28,8 @@ struct MixedPass {
     int smem = 0, threads = 256;
     int64_t blocks = 0;
 };
+
+static bool is_fp64(const fftc_plan_s *p) { return p->precision == FFTC_FP64; }
 
 struct MixedState {
     int npasses = 0;
@@ -101,8 +105,9 @@ static bool check_div(const FastDiv &f, uint64_t limit) {
 }
 
 template <int KIND, int LIN, int LOUT>
-static MixedKernel mixed_kernel(int nt) {
-    return nt == 512 ? &k_mixed<KIND, LIN, LOUT, 512> : &k_mixed<KIND, LIN, LOUT, 256>;
+static MixedKernel mixed_kernel(int nt, bool fp64) {
+    if (fp64) return nt == 512 ? &k_mixed<KIND, LIN, LOUT, 512, double2> : &k_mixed<KIND, LIN, LOUT, 256, double2>;
+    return nt == 512 ? &k_mixed<KIND, LIN, LOUT, 512, float2> : &k_mixed<KIND, LIN, LOUT, 256, float2>;
 }
 
 // stage tables of a line: stage s holds w_{Ns r}^{t k} at (t - 1) Ns + k (t < r, k < Ns)
@@ -110,6 +115,7 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
                                     int64_t lpt) {
     const std::vector<int> rad = mixed_radices(L);
     if (rad.empty() || (int)rad.size() > kMixedMaxStages) return FFTC_ERR_UNSUPPORTED_SIZE;
+    const bool fp64 = is_fp64(p);
     MixedArgs &a = mp.args;
     a.L = (int32_t)L;
     a.C = C;
@@ -117,13 +123,14 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     // single pass: lines back to back (flat copies); four-step: an odd pitch for column access
     a.pitch = (int32_t)L + (kind != KIND_ROWS && C > 1 && (L & 1) == 0 ? 1 : 0);
     a.lpt = (int32_t)lpt;
-    std::vector<float2> tw;
+    std::vector<float2> tw;     // FP32 tables
+    std::vector<double2> tw64;  // FP64 tables (the same entries, unrounded)
     int64_t ns = 1;
     for (int s = 0; s < a.nst; ++s) {
         const int r = rad[(size_t)s];
         a.radix[s] = (int8_t)r;
         a.ns[s] = (int32_t)ns;
-        a.tw_off[s] = (int32_t)tw.size();
+        a.tw_off[s] = (int32_t)(fp64 ? tw64.size() : tw.size());
         a.div_lr[s] = make_div((uint32_t)(L / r));
         a.div_ns[s] = make_div((uint32_t)ns);
         if (!check_div(a.div_lr[s], (uint64_t)C * L) || !check_div(a.div_ns[s], (uint64_t)L))
@@ -133,7 +140,8 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
                 for (int64_t k = 0; k < ns; ++k) {
                     double c, sn;
                     unit_root((int64_t)t * k, ns * r, &c, &sn);
-                    tw.push_back(make_float2((float)c, (float)-sn));
+                    if (fp64) tw64.push_back(make_double2(c, -sn));
+                    else tw.push_back(make_float2((float)c, (float)-sn));
                 }
         ns *= r;
     }
@@ -144,25 +152,27 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     if (!check_div(a.div_L, tile) || !check_div(a.div_C, tile) ||
         !check_div(a.div_lpt, (uint64_t)a.p.total_lines + (uint64_t)C))
         return FFTC_ERR_UNSUPPORTED_SIZE;
-    if (!tw.empty()) {
+    if (!tw.empty() || !tw64.empty()) {
         void *d = nullptr;
-        if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
-        a.p.tw = (const float2 *)d;
+        const cudaError_t e = fp64 ? plan_upload(p, tw64.data(), tw64.size() * sizeof(double2), &d)
+                                   : plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d);
+        if (e != cudaSuccess) return FFTC_ERR_ALLOC;
+        a.p.tw = (const float2 *)d;  // reinterpreted as double2 by the FP64 kernels
     }
     // 512 threads for tiles of more than 4096 elements (one or two CTAs per SM)
     const int nt = tile > 4096 ? 512 : 256;
     mp.threads = nt;
     if (kind == KIND_ROWS)
-        mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_ROWS, LAYOUT_IL, LAYOUT_IL>(nt)
-                                     : mixed_kernel<KIND_ROWS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt);
+        mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_ROWS, LAYOUT_IL, LAYOUT_IL>(nt, fp64)
+                                     : mixed_kernel<KIND_ROWS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt, fp64);
     else if (kind == KIND_COLS)
-        mp.kernel = lin == LAYOUT_IL       ? mixed_kernel<KIND_COLS, LAYOUT_IL, LAYOUT_IL>(nt)
-                    : lout == LAYOUT_SPLIT ? mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt)
-                                           : mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL>(nt);
+        mp.kernel = lin == LAYOUT_IL       ? mixed_kernel<KIND_COLS, LAYOUT_IL, LAYOUT_IL>(nt, fp64)
+                    : lout == LAYOUT_SPLIT ? mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt, fp64)
+                                           : mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL>(nt, fp64);
     else
-        mp.kernel = lout == LAYOUT_IL ? mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_IL>(nt)
-                                      : mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT>(nt);
-    mp.smem = (((C * a.pitch + 1) & ~1) + C * a.pitch) * (int)sizeof(float2);
+        mp.kernel = lout == LAYOUT_IL ? mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_IL>(nt, fp64)
+                                      : mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT>(nt, fp64);
+    mp.smem = (((C * a.pitch + 1) & ~1) + C * a.pitch) * (int)(fp64 ? sizeof(double2) : sizeof(float2));
     if (mp.smem > 48 * 1024) {
         // the dynamic shared memory of one kernel differs from plan to plan: allow the
         // device's maximum once (a smaller limit set for a later plan would break an
@@ -180,10 +190,14 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     return FFTC_OK;
 }
 
-static int mixed_lines(int64_t L) { return (int)std::max<int64_t>(1, kMixedTile / L); }
+static int mixed_lines(int64_t L, bool fp64 = false) {
+    return (int)std::max<int64_t>(1, (fp64 ? kMixedTile64 : kMixedTile) / L);
+}
 
 fftc_status mixed_build(fftc_plan_s *p) {
-    if (p->precision != FFTC_FP32) return FFTC_ERR_UNSUPPORTED_SIZE;
+    if (p->precision != FFTC_FP32 && p->precision != FFTC_FP64) return FFTC_ERR_UNSUPPORTED_SIZE;
+    const bool fp64 = is_fp64(p);
+    const int64_t single = fp64 ? kMixedSinglePass64 : kMixedSinglePass;
     MixedState *ms = new (std::nothrow) MixedState();
     if (!ms) return FFTC_ERR_ALLOC;
     p->mixed = ms;
@@ -195,7 +209,7 @@ fftc_status mixed_build(fftc_plan_s *p) {
     if (plan_alloc(p, 16, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     p->d_err = (int *)d;
     if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
-    if (n <= kMixedSinglePass) {
+    if (n <= single) {
         ms->npasses = p->npasses = 1;
         MixedPass &mp = ms->pass[0];
         PassParams &b = mp.args.p;
@@ -207,29 +221,34 @@ fftc_status mixed_build(fftc_plan_s *p) {
         b.in_elem = b.out_elem = 1;
         // a multiple of 4 lines per tile when there are several, so every tile starts 16-byte
         // aligned in both layouts
-        const int C = mixed_lines(n);
+        const int C = mixed_lines(n, fp64);
         return mixed_pass_setup(p, mp, n, C >= 4 ? C / 4 * 4 : C, KIND_ROWS, lay, lay, 1);
     }
     // n = M K with both factors at most one CTA's line, M as close to sqrt(n) as possible
     int64_t M = 0;
-    for (int64_t m = 2; m <= kMixedSinglePass; ++m)
-        if (n % m == 0 && n / m <= kMixedSinglePass &&
+    for (int64_t m = 2; m <= single; ++m)
+        if (n % m == 0 && n / m <= single &&
             (M == 0 || std::llabs((long long)(m * m - n)) < std::llabs((long long)(M * M - n))))
             M = m;
     if (M == 0) return FFTC_ERR_UNSUPPORTED_SIZE;
     const int64_t K = n / M;
     ms->npasses = p->npasses = 2;
-    if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
+    if (plan_alloc(p, (size_t)(n * B) * esz, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     p->workspace = (float2 *)d;
     {  // the inter-pass diagonal D of Eq. 1 in pass-1 order: entry t' K + b = w_N^(b t')
-        std::vector<float2> full((size_t)n);
+        std::vector<float2> full(fp64 ? 0 : (size_t)n);
+        std::vector<double2> full64(fp64 ? (size_t)n : 0);
         for (int64_t tp = 0; tp < M; ++tp)
             for (int64_t b = 0; b < K; ++b) {
                 double c, s;
                 unit_root(tp * b, n, &c, &s);
-                full[(size_t)(tp * K + b)] = make_float2((float)c, (float)-s);
+                if (fp64) full64[(size_t)(tp * K + b)] = make_double2(c, -s);
+                else full[(size_t)(tp * K + b)] = make_float2((float)c, (float)-s);
             }
-        if (plan_upload(p, full.data(), full.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        const cudaError_t e = fp64 ? plan_upload(p, full64.data(), full64.size() * sizeof(double2), &d)
+                                   : plan_upload(p, full.data(), full.size() * sizeof(float2), &d);
+        if (e != cudaSuccess) return FFTC_ERR_ALLOC;
         p->tw2_full = (float2 *)d;
     }
     {  // pass 1: K columns of length M at stride K, times the diagonal, into the workspace
@@ -243,8 +262,8 @@ fftc_status mixed_build(fftc_plan_s *p) {
         b.in_line = b.out_line = 1;
         b.in_elem = b.out_elem = K;
         b.tw2_full = p->tw2_full;
-        fftc_status s = mixed_pass_setup(p, mp, M, (int)std::min<int64_t>(K, mixed_lines(M)), KIND_COLS, lay,
-                                         LAYOUT_IL, K);
+        fftc_status s = mixed_pass_setup(p, mp, M, (int)std::min<int64_t>(K, mixed_lines(M, fp64)), KIND_COLS,
+                                         lay, LAYOUT_IL, K);
         if (s != FFTC_OK) return s;
     }
     {  // pass 2: M rows of length K, stored transposed (output k1 + M k2)
@@ -259,7 +278,8 @@ fftc_status mixed_build(fftc_plan_s *p) {
         b.in_elem = 1;
         b.out_line = 1;
         b.out_elem = M;
-        return mixed_pass_setup(p, mp, K, (int)std::min<int64_t>(M, mixed_lines(K)), KIND_ROWST, LAYOUT_IL, lay, M);
+        return mixed_pass_setup(p, mp, K, (int)std::min<int64_t>(M, mixed_lines(K, fp64)), KIND_ROWST, LAYOUT_IL,
+                                lay, M);
     }
 }
 

@@ -1,4 +1,5 @@
-// Mixed-radix Stockham pass for n = 2^a 3^b 5^c 7^d (not a power of two).
+// Runtime-radix Stockham pass: FP32 for n = 2^a 3^b 5^c 7^d that are not powers of two,
+// FP64 (complex128) for every supported n. The element type V is float2 or double2.
 //
 // One CTA transforms C lines of length L held in shared memory. The radices r_s of the
 // line (from {16, 15, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2}, product L) are runtime values,
@@ -17,6 +18,8 @@
 // division by invariant integers instead of shifts.
 #pragma once
 
+#include <type_traits>
+
 #include "fftc_ctrig.h"
 #include "fftc_device.cuh"
 #include "fftc_internal.h"
@@ -24,6 +27,24 @@
 namespace fftc {
 
 constexpr int kMixedMaxStages = 24;
+
+template <typename V>
+struct CplxT;
+template <>
+struct CplxT<float2> {
+    using S = float;
+    __host__ __device__ static float2 make(float x, float y) { return make_float2(x, y); }
+};
+template <>
+struct CplxT<double2> {
+    using S = double;
+    __host__ __device__ static double2 make(double x, double y) { return make_double2(x, y); }
+};
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
 
 
 // Unsigned division by an invariant d for dividends below 2^31 (the round-up multiply
@@ -69,35 +90,46 @@ __host__ __device__ constexpr float mixed_sin(int r, int m) {
 // b_j = x_j - x_{R-j} (j = 1 .. (R-1)/2),
 //   X_k     = x_0 + sum_j cos(2 pi jk/R) a_j - i sum_j sin(2 pi jk/R) b_j
 //   X_{R-k} = x_0 + sum_j cos(2 pi jk/R) a_j + i sum_j sin(2 pi jk/R) b_j.
-template <int R>
-__device__ __forceinline__ void dft_odd(float2 *x) {
+// odd-radix constants: FP32 from the pinned literals, FP64 from the compile-time series
+template <typename V>
+__host__ __device__ constexpr typename CplxT<V>::S odd_cos(int r, int m) {
+    return std::is_same<V, float2>::value ? (typename CplxT<V>::S)mixed_cos(r, m) : (typename CplxT<V>::S)ct_cos(m, r);
+}
+template <typename V>
+__host__ __device__ constexpr typename CplxT<V>::S odd_sin(int r, int m) {
+    return std::is_same<V, float2>::value ? (typename CplxT<V>::S)mixed_sin(r, m) : (typename CplxT<V>::S)ct_sin(m, r);
+}
+
+template <int R, typename V>
+__device__ __forceinline__ void dft_odd(V *x) {
+    using S = typename CplxT<V>::S;
     constexpr int H = (R - 1) / 2;
-    float2 a[H + 1], b[H + 1];
-    float2 s0 = x[0];
+    V a[H + 1], b[H + 1];
+    V s0 = x[0];
 #pragma unroll
     for (int j = 1; j <= H; ++j) {
         a[j] = cadd(x[j], x[R - j]);
         b[j] = csub(x[j], x[R - j]);
         s0 = cadd(s0, a[j]);
     }
-    float2 y[R];
+    V y[R];
     y[0] = s0;
 #pragma unroll
     for (int k = 1; k <= H; ++k) {
-        float2 A = x[0], B = make_float2(0.f, 0.f);
+        V A = x[0], B = CplxT<V>::make(0, 0);
 #pragma unroll
         for (int j = 1; j <= H; ++j) {
             const int m = (j * k) % R;  // compile-time
-            const float c = m <= H ? mixed_cos(R, m) : mixed_cos(R, R - m);
-            const float s = m <= H ? mixed_sin(R, m) : -mixed_sin(R, R - m);
+            const S c = m <= H ? odd_cos<V>(R, m) : odd_cos<V>(R, R - m);
+            const S s = m <= H ? odd_sin<V>(R, m) : -odd_sin<V>(R, R - m);
             A.x += c * a[j].x;
             A.y += c * a[j].y;
             B.x += s * b[j].x;
             B.y += s * b[j].y;
         }
         // -i B = (B.y, -B.x)
-        y[k] = make_float2(A.x + B.y, A.y - B.x);
-        y[R - k] = make_float2(A.x - B.y, A.y + B.x);
+        y[k] = CplxT<V>::make(A.x + B.y, A.y - B.x);
+        y[R - k] = CplxT<V>::make(A.x - B.y, A.y + B.x);
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = y[k];
@@ -107,55 +139,56 @@ __host__ __device__ constexpr int ct_spf(int r) { return r % 2 == 0 ? 2 : r % 3 
 
 // x *= w_R^e (forward, w_R = exp(-2 pi i / R)) with a compile-time exponent: quarter turns
 // exactly, other angles from the compile-time cos / sin
-template <int R, int E>
-__device__ __forceinline__ float2 mul_wr(float2 x) {
+template <int R, int E, typename V>
+__device__ __forceinline__ V mul_wr(V x) {
+    using S = typename CplxT<V>::S;
     constexpr int e = E % R;
     if constexpr (e == 0) {
         return x;
     } else if constexpr ((4 * e) % R == 0) {
         constexpr int q = 4 * e / R;  // quarter turns
-        if constexpr (q == 1) return make_float2(x.y, -x.x);
-        else if constexpr (q == 2) return make_float2(-x.x, -x.y);
-        else return make_float2(-x.y, x.x);
+        if constexpr (q == 1) return CplxT<V>::make(x.y, -x.x);
+        else if constexpr (q == 2) return CplxT<V>::make(-x.x, -x.y);
+        else return CplxT<V>::make(-x.y, x.x);
     } else {
-        constexpr float c = (float)ct_cos(e, R), s = (float)ct_sin(e, R);
-        return make_float2(x.x * c + x.y * s, x.y * c - x.x * s);
+        constexpr S c = (S)ct_cos(e, R), s = (S)ct_sin(e, R);
+        return CplxT<V>::make(x.x * c + x.y * s, x.y * c - x.x * s);
     }
 }
 
-template <int R>
-__device__ __forceinline__ void dft_small(float2 *v);
+template <int R, typename V>
+__device__ __forceinline__ void dft_small(V *v);
 
 // DFT_R for composite R = P Q in registers (Eq. 1 once more): input j = a + P b; the Q-point
 // DFTs over b for every a, the twiddles w_R^(a q), then the P-point DFTs over a, giving
 // output q + Q k
-template <int P, int Q, int A, int q = 0>
-__device__ __forceinline__ void ct_scatter(float2 *v, const float2 *t) {
+template <int P, int Q, int A, typename V, int q = 0>
+__device__ __forceinline__ void ct_scatter(V *v, const V *t) {
     if constexpr (q < Q) {
         v[A + P * q] = mul_wr<P * Q, A * q>(t[q]);
-        ct_scatter<P, Q, A, q + 1>(v, t);
+        ct_scatter<P, Q, A, V, q + 1>(v, t);
     }
 }
 
-template <int P, int Q, int A = 0>
-__device__ __forceinline__ void ct_inner(float2 *v) {
+template <int P, int Q, typename V, int A = 0>
+__device__ __forceinline__ void ct_inner(V *v) {
     if constexpr (A < P) {
-        float2 t[Q];
+        V t[Q];
 #pragma unroll
         for (int b = 0; b < Q; ++b) t[b] = v[A + P * b];
         dft_small<Q>(t);
-        ct_scatter<P, Q, A>(v, t);
-        ct_inner<P, Q, A + 1>(v);
+        ct_scatter<P, Q, A, V>(v, t);
+        ct_inner<P, Q, V, A + 1>(v);
     }
 }
 
-template <int P, int Q>
-__device__ __forceinline__ void dft_ct(float2 *v) {
-    ct_inner<P, Q>(v);
-    float2 y[P * Q];
+template <int P, int Q, typename V>
+__device__ __forceinline__ void dft_ct(V *v) {
+    ct_inner<P, Q, V>(v);
+    V y[P * Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        float2 u[P];
+        V u[P];
 #pragma unroll
         for (int a = 0; a < P; ++a) u[a] = v[a + P * q];
         dft_small<P>(u);
@@ -166,24 +199,34 @@ __device__ __forceinline__ void dft_ct(float2 *v) {
     for (int i = 0; i < P * Q; ++i) v[i] = y[i];
 }
 
-template <int R>
-__device__ __forceinline__ void dft_small(float2 *v) {
-    if constexpr ((R & (R - 1)) == 0) dft<R>(v);
-    else if constexpr (ct_spf(R) == R) dft_odd<R>(v);
-    else dft_ct<ct_spf(R), R / ct_spf(R)>(v);
+template <int R, typename V>
+__device__ __forceinline__ void dft_small(V *v) {
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2) {
+        const V a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr ((R & (R - 1)) == 0 && std::is_same<V, float2>::value) {
+        dft<R>(v);  // FP32: the radix-2 network with its exact constant twiddles
+    } else if constexpr (ct_spf(R) == R) {
+        dft_odd<R>(v);
+    } else {
+        dft_ct<ct_spf(R), R / ct_spf(R), V>(v);
+    }
 }
 
-template <int R, int NT>
-__device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const float2 *src, float2 *dst) {
+template <int R, int NT, typename V>
+__device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *src, V *dst) {
     const int L = a.L, Lr = L / R, Ns = a.ns[s];
     const int G = a.C * Lr;
-    const float2 *tw = a.p.tw + a.tw_off[s];
+    const V *tw = reinterpret_cast<const V *>(a.p.tw) + a.tw_off[s];
 #pragma unroll 2
     for (int gi = threadIdx.x; gi < G; gi += NT) {
         const int c = (int)fdiv((uint32_t)gi, a.div_lr[s]);
         const int j = gi - c * Lr;
-        const float2 *line = src + c * a.pitch;
-        float2 v[R];
+        const V *line = src + c * a.pitch;
+        V v[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = line[j + t * Lr];
         const int jq = (int)fdiv((uint32_t)j, a.div_ns[s]);
@@ -193,7 +236,7 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const flo
             for (int t = 1; t < R; ++t) v[t] = cmul(v[t], __ldg(tw + (t - 1) * Ns + jm));
         }
         dft_small<R>(v);
-        float2 *out = dst + c * a.pitch;
+        V *out = dst + c * a.pitch;
         const int o = jq * Ns * R + jm;
 #pragma unroll
         for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
@@ -220,6 +263,41 @@ __device__ __forceinline__ void tile_coord(const MixedArgs &a, int f, int &c, in
 // Single pass: the tile's lines are back to back in HBM and in shared memory (pitch L), so
 // the copy is flat, in 16-byte vectors when the tile starts 16-byte aligned in every plane
 // (always for tiles of 4 or more lines: their line count is a multiple of 4).
+// FP64 single pass: element-wise copies (a complex128 element is itself a 16-byte vector)
+template <int LAY, int NT, bool LOAD>
+__device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, double2 *sm) {
+    const PassParams &p = a.p;
+    const int64_t lines = min((int64_t)a.C, p.total_lines - g0);
+    const int T = (int)lines * a.L;
+    const int64_t base = g0 * a.L;
+    const int cj = LOAD ? p.conj_in : p.conj_out;
+    const double *pin = reinterpret_cast<const double *>(p.in);
+    double *pout = reinterpret_cast<double *>(p.out);
+#pragma unroll 4
+    for (int f = threadIdx.x; f < T; f += NT) {
+        if constexpr (LOAD) {
+            double2 x;
+            if constexpr (LAY == LAYOUT_IL) {
+                x = __ldcs(reinterpret_cast<const double2 *>(pin) + base + f);
+            } else {
+                x.x = __ldcs(pin + base + f);
+                x.y = __ldcs(pin + p.in_plane + base + f);
+            }
+            if (cj) x.y = -x.y;
+            sm[f] = x;
+        } else {
+            double2 x = sm[f];
+            if (cj) x.y = -x.y;
+            if constexpr (LAY == LAYOUT_IL) {
+                __stcs(reinterpret_cast<double2 *>(pout) + base + f, x);
+            } else {
+                __stcs(pout + base + f, x.x);
+                __stcs(pout + p.out_plane + base + f, x.y);
+            }
+        }
+    }
+}
+
 template <int LAY, int NT, bool LOAD>
 __device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, float2 *sm) {
     const PassParams &p = a.p;
@@ -299,17 +377,19 @@ __device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, float2
     }
 }
 
-template <int KIND, int LIN, int NT>
-__device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, float2 *sm) {
+template <int KIND, int LIN, int NT, typename V>
+__device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, V *sm) {
+    using S = typename CplxT<V>::S;
     const PassParams &p = a.p;
     const int T = a.C * a.L;
     const int cj = p.conj_in;
+    const S *pin = reinterpret_cast<const S *>(p.in);
     for (int base = 0; base < T; base += NT * kMixedBatch) {
-        float2 x[kMixedBatch];
+        V x[kMixedBatch];
 #pragma unroll
         for (int i = 0; i < kMixedBatch; ++i) {
             const int f = base + i * NT + (int)threadIdx.x;
-            x[i] = make_float2(0.f, 0.f);
+            x[i] = CplxT<V>::make(0, 0);
             int c, e;
             tile_coord<KIND>(a, f, c, e);
             const int64_t g = g0 + c;
@@ -317,10 +397,10 @@ __device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, float
                 const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
                 const int64_t off = tr * p.in_tr + l * p.in_line + (int64_t)e * p.in_elem;
                 if constexpr (LIN == LAYOUT_IL) {
-                    x[i] = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
+                    x[i] = __ldcs(reinterpret_cast<const V *>(pin) + off);
                 } else {
-                    x[i].x = __ldcs(p.in + off);
-                    x[i].y = __ldcs(p.in + p.in_plane + off);
+                    x[i].x = __ldcs(pin + off);
+                    x[i].y = __ldcs(pin + p.in_plane + off);
                 }
             }
         }
@@ -337,9 +417,11 @@ __device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, float
     }
 }
 
-template <int KIND, int LOUT, int NT>
-__device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, const float2 *sm) {
+template <int KIND, int LOUT, int NT, typename V>
+__device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, const V *sm) {
+    using S = typename CplxT<V>::S;
     const PassParams &p = a.p;
+    S *pout = reinterpret_cast<S *>(p.out);
     const int L = a.L, C = a.C, T = C * L;
     const int cj = p.conj_out;
 #pragma unroll 4
@@ -355,35 +437,36 @@ __device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, cons
         const int64_t g = g0 + c;
         if (g >= p.total_lines) continue;
         const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
-        float2 x = sm[c * a.pitch + e];
+        V x = sm[c * a.pitch + e];
         if constexpr (KIND == KIND_COLS) {
             // inter-pass diagonal of Eq. 1: column l, output row e: w_N^(l e) (four-step only;
             // a strided axis of a multidimensional transform has none)
-            if (p.tw2_full) x = cmul(x, __ldg(p.tw2_full + (int64_t)e * a.lpt + l));
+            if (p.tw2_full) x = cmul(x, __ldg(reinterpret_cast<const V *>(p.tw2_full) + (int64_t)e * a.lpt + l));
         }
         if (cj) x.y = -x.y;
         const int64_t off = tr * p.out_tr + l * p.out_line + (int64_t)e * p.out_elem;
         if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
-            __stcg(reinterpret_cast<float2 *>(p.out) + off, x);  // workspace: keep it in L2
+            __stcg(reinterpret_cast<V *>(pout) + off, x);  // workspace: keep it in L2
         } else if constexpr (LOUT == LAYOUT_IL) {
-            __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
+            __stcs(reinterpret_cast<V *>(pout) + off, x);
         } else {
-            __stcs(p.out + off, x.x);
-            __stcs(p.out + p.out_plane + off, x.y);
+            __stcs(pout + off, x.x);
+            __stcs(pout + p.out_plane + off, x.y);
         }
     }
 }
 
-template <int KIND, int LIN, int LOUT, int NT>
+template <int KIND, int LIN, int LOUT, int NT, typename V>
 __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs a) {
-    extern __shared__ float2 sm_mixed[];
+    extern __shared__ __align__(16) unsigned char sm_mixed_raw[];
+    V *sm_mixed = reinterpret_cast<V *>(sm_mixed_raw);
     // the second buffer starts 16-byte aligned (the single-pass copies move 16-byte vectors)
-    float2 *buf0 = sm_mixed, *buf1 = sm_mixed + ((a.C * a.pitch + 1) & ~1);
+    V *buf0 = sm_mixed, *buf1 = sm_mixed + ((a.C * a.pitch + 1) & ~1);
     const int64_t g0 = (int64_t)blockIdx.x * a.C;
     if constexpr (KIND == KIND_ROWS) rows_copy<LIN, NT, true>(a, g0, buf0);
     else mixed_load<KIND, LIN, NT>(a, g0, buf0);
     __syncthreads();
-    float2 *src = buf0, *dst = buf1;
+    V *src = buf0, *dst = buf1;
     for (int s = 0; s < a.nst; ++s) {
         switch (a.radix[s]) {
             case 2: mixed_stage<2, NT>(a, s, src, dst); break;
@@ -401,7 +484,7 @@ __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs 
             default: mixed_stage<16, NT>(a, s, src, dst); break;
         }
         __syncthreads();
-        float2 *t = src;
+        V *t = src;
         src = dst;
         dst = t;
     }

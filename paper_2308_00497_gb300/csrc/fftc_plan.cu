@@ -317,7 +317,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
 }
 
 fftc_status plan_build(fftc_plan_s *p) {
-    if ((p->n & (p->n - 1)) != 0) return mixed_build(p);
+    if ((p->n & (p->n - 1)) != 0 || p->precision == FFTC_FP64) return mixed_build(p);
     return plan_build_passes(p);
 }
 
