@@ -432,9 +432,38 @@ def run_extras(args, dev) -> dict:
     del xs, ts, xf
     out["mixed_radix"] = run_mixed(dev, reps)
     out["multidim"] = run_nd(dev, reps)
+    out["fp64"] = run_fp64(dev, reps)
     if not args.no_precision:
         out["precision"] = run_precision(args, dev, reps)
     return out
+
+
+FP64_SIZES = [1024, 1000, 1 << 16, 1 << 20]
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (CUDA cores); no measured FP64 figure exists
+
+
+def run_fp64(dev, reps: int) -> dict:
+    """complex128 transforms, n * batch = 2^25 (512 MiB per buffer), forward, interleaved:
+    ms, GFLOP/s (5 n log2 n), the fraction of the nominal FP64 rate, and the HBM fraction
+    per pass (32 B per element and pass)."""
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    res = []
+    E = ELEMS // 2
+    for n in FP64_SIZES:
+        B = E // n
+        x = torch.randn(B, n, dtype=torch.complex128, device=dev)
+        y = torch.empty_like(x)
+        p = fc.Plan(n, B, "interleaved", False, precision="fp64", device=dev)
+        t = _time_ms(lambda: p.execute(x, y), reps)
+        gf = flops(n, B) / (t * 1e-3) / 1e9
+        res.append({"n": n, "batch": B, "passes": p.info()[0], "ms": round(t, 4), "gflops": round(gf, 1),
+                    "fp64_frac_nominal": round(gf / (FP64_PEAK_TFLOPS * 1e3), 4),
+                    "hbm_frac_per_pass": round(32.0 * n * B * p.info()[0] / (t * 1e-3) / 1e9 / peaks()[0], 4)})
+        del x, y, p
+    return {"workload": "FP64 complex128 C2C, n * batch = 2^25, forward, interleaved", "bound": "alu (FP64)",
+            "peak_tflops_nominal": FP64_PEAK_TFLOPS, "results": res}
 
 
 ND_SHAPES = [(1024, 1024), (4096, 4096), (1000, 1000), (256, 256, 256), (64, 64, 64)]
