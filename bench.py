@@ -98,6 +98,18 @@ def stored_traffic(kind: str):
     return table.get(kind)
 
 
+def _nvtx(push: bool, name: str = "") -> None:
+    """Open / close an NVTX range (a no-op where torch has no NVTX support)."""
+    try:
+        import torch
+        if push:
+            torch.cuda.nvtx.range_push(name)
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:  # pragma: no cover
+        pass
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -262,10 +274,12 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
         dist.barrier()
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _nvtx(True, "timed_sweep")  # lets a profiler capture exactly the timed launches
     t0.record()
     for _ in range(args.steps):
         step()
     t1.record()
+    _nvtx(False)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     if dist:
