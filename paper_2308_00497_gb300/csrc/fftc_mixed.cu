@@ -20,7 +20,7 @@ static const int kMixedTile = 4096;        // FP32 elements per CTA tile for sho
 static const int kMixedSinglePass64 = 4096;  // the same for FP64 (16-byte elements)
 static const int kMixedTile64 = 2048;
 
-typedef void (*MixedKernel)(MixedArgs);
+extern const MixedKernel kMixedRowsF32[2][2], kMixedRowsF64[2][2], kMixedStridedF32[5][2], kMixedStridedF64[5][2];
 
 struct MixedPass {
     MixedArgs args;
@@ -104,10 +104,15 @@ static bool check_div(const FastDiv &f, uint64_t limit) {
     return true;
 }
 
-template <int KIND, int LIN, int LOUT>
-static MixedKernel mixed_kernel(int nt, bool fp64) {
-    if (fp64) return nt == 512 ? &k_mixed<KIND, LIN, LOUT, 512, double2> : &k_mixed<KIND, LIN, LOUT, 256, double2>;
-    return nt == 512 ? &k_mixed<KIND, LIN, LOUT, 512, float2> : &k_mixed<KIND, LIN, LOUT, 256, float2>;
+// the compiled variant for (kind, layouts, CTA size, element type); NULL if none
+static MixedKernel mixed_kernel(int kind, int lin, int lout, int nt, bool fp64) {
+    const int w = nt == 512 ? 1 : 0;
+    if (kind == KIND_ROWS) return (fp64 ? kMixedRowsF64 : kMixedRowsF32)[lin == LAYOUT_IL ? 0 : 1][w];
+    int v = -1;
+    if (kind == KIND_COLS) v = lin == LAYOUT_IL ? 0 : (lout == LAYOUT_IL ? 1 : 2);
+    else if (kind == KIND_ROWST) v = lout == LAYOUT_IL ? 3 : 4;
+    if (v < 0 || (kind == KIND_COLS && lin == LAYOUT_IL && lout != LAYOUT_IL)) return nullptr;
+    return (fp64 ? kMixedStridedF64 : kMixedStridedF32)[v][w];
 }
 
 // stage tables of a line: stage s holds w_{Ns r}^{t k} at (t - 1) Ns + k (t < r, k < Ns)
@@ -123,6 +128,7 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     // single pass: lines back to back (flat copies); four-step: an odd pitch for column access
     a.pitch = (int32_t)L + (kind != KIND_ROWS && C > 1 && (L & 1) == 0 ? 1 : 0);
     a.lpt = (int32_t)lpt;
+    a.flat = kind == KIND_ROWS && lin == LAYOUT_SPLIT && !fp64 && L <= 128;  // measured crossover
     std::vector<float2> tw;     // FP32 tables
     std::vector<double2> tw64;  // FP64 tables (the same entries, unrounded)
     int64_t ns = 1;
@@ -162,16 +168,8 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     // 512 threads for tiles of more than 4096 elements (one or two CTAs per SM)
     const int nt = tile > 4096 ? 512 : 256;
     mp.threads = nt;
-    if (kind == KIND_ROWS)
-        mp.kernel = lin == LAYOUT_IL ? mixed_kernel<KIND_ROWS, LAYOUT_IL, LAYOUT_IL>(nt, fp64)
-                                     : mixed_kernel<KIND_ROWS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt, fp64);
-    else if (kind == KIND_COLS)
-        mp.kernel = lin == LAYOUT_IL       ? mixed_kernel<KIND_COLS, LAYOUT_IL, LAYOUT_IL>(nt, fp64)
-                    : lout == LAYOUT_SPLIT ? mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_SPLIT>(nt, fp64)
-                                           : mixed_kernel<KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL>(nt, fp64);
-    else
-        mp.kernel = lout == LAYOUT_IL ? mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_IL>(nt, fp64)
-                                      : mixed_kernel<KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT>(nt, fp64);
+    mp.kernel = mixed_kernel(kind, lin, lout, nt, fp64);
+    if (!mp.kernel) return FFTC_ERR_UNSUPPORTED_SIZE;
     mp.smem = (((C * a.pitch + 1) & ~1) + C * a.pitch) * (int)(fp64 ? sizeof(double2) : sizeof(float2));
     if (mp.smem > 48 * 1024) {
         // the dynamic shared memory of one kernel differs from plan to plan: allow the

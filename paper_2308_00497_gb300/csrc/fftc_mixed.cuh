@@ -68,6 +68,7 @@ struct MixedArgs {
                              // inter-pass diagonal (tw2_full, columns kind), error word
     int32_t L, C, nst, pitch;
     int32_t lpt;             // lines per transform (1 rows, K columns, M transposed rows)
+    int32_t flat;            // FP32 split single pass: move the tile with flat vector copies
     FastDiv div_lpt, div_L, div_C;
     int8_t radix[kMixedMaxStages];
     int32_t ns[kMixedMaxStages], tw_off[kMixedMaxStages];
@@ -216,8 +217,12 @@ __device__ __forceinline__ void dft_small(V *v) {
     }
 }
 
-template <int R, int NT, typename V>
-__device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *src, V *dst) {
+// One stage over the tile. IO bit 0: the stage reads HBM (the single pass's first stage,
+// line g0 + c at element offset (g0 + c) L, coalesced over j), bit 1: it writes HBM (the
+// last stage, whose output index j + t Ns is coalesced over j); otherwise shared memory.
+template <int R, int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL>
+__device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *src, V *dst, int64_t g0 = 0) {
+    using S = typename CplxT<V>::S;
     const int L = a.L, Lr = L / R, Ns = a.ns[s];
     const int G = a.C * Lr;
     const V *tw = reinterpret_cast<const V *>(a.p.tw) + a.tw_off[s];
@@ -225,10 +230,30 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
     for (int gi = threadIdx.x; gi < G; gi += NT) {
         const int c = (int)fdiv((uint32_t)gi, a.div_lr[s]);
         const int j = gi - c * Lr;
-        const V *line = src + c * a.pitch;
         V v[R];
+        const bool live = !(IO & 3) || g0 + c < a.p.total_lines;
+        if constexpr (IO & 1) {
+            const int64_t b = (g0 + c) * L + j;
+            const S *pin = reinterpret_cast<const S *>(a.p.in);
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = line[j + t * Lr];
+            for (int t = 0; t < R; ++t) {
+                V x = CplxT<V>::make(0, 0);
+                if (live) {
+                    if constexpr (LIN == LAYOUT_IL) {
+                        x = __ldcs(reinterpret_cast<const V *>(pin) + b + t * Lr);
+                    } else {
+                        x.x = __ldcs(pin + b + t * Lr);
+                        x.y = __ldcs(pin + a.p.in_plane + b + t * Lr);
+                    }
+                }
+                if (a.p.conj_in) x.y = -x.y;
+                v[t] = x;
+            }
+        } else {
+            const V *line = src + c * a.pitch;
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = line[j + t * Lr];
+        }
         const int jq = (int)fdiv((uint32_t)j, a.div_ns[s]);
         const int jm = j - jq * Ns;
         if (Ns > 1) {
@@ -236,10 +261,47 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
             for (int t = 1; t < R; ++t) v[t] = cmul(v[t], __ldg(tw + (t - 1) * Ns + jm));
         }
         dft_small<R>(v);
-        V *out = dst + c * a.pitch;
         const int o = jq * Ns * R + jm;
+        if constexpr (IO & 2) {
+            if (live) {
+                const int64_t b = (g0 + c) * L + o;
+                S *pout = reinterpret_cast<S *>(a.p.out);
 #pragma unroll
-        for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
+                for (int t = 0; t < R; ++t) {
+                    V x = v[t];
+                    if (a.p.conj_out) x.y = -x.y;
+                    if constexpr (LOUT == LAYOUT_IL) {
+                        __stcs(reinterpret_cast<V *>(pout) + b + t * Ns, x);
+                    } else {
+                        __stcs(pout + b + t * Ns, x.x);
+                        __stcs(pout + a.p.out_plane + b + t * Ns, x.y);
+                    }
+                }
+            }
+        } else {
+            V *out = dst + c * a.pitch;
+#pragma unroll
+            for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
+        }
+    }
+}
+
+template <int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL>
+__device__ __forceinline__ void run_stage(const MixedArgs &a, int s, const V *src, V *dst, int64_t g0 = 0) {
+    switch (a.radix[s]) {
+        case 2: mixed_stage<2, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 3: mixed_stage<3, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 4: mixed_stage<4, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 5: mixed_stage<5, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 6: mixed_stage<6, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 7: mixed_stage<7, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 8: mixed_stage<8, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 9: mixed_stage<9, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 10: mixed_stage<10, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 12: mixed_stage<12, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 14: mixed_stage<14, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        case 15: mixed_stage<15, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
+        default: mixed_stage<16, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
     }
 }
 
@@ -260,44 +322,9 @@ __device__ __forceinline__ void tile_coord(const MixedArgs &a, int f, int &c, in
     }
 }
 
-// Single pass: the tile's lines are back to back in HBM and in shared memory (pitch L), so
-// the copy is flat, in 16-byte vectors when the tile starts 16-byte aligned in every plane
-// (always for tiles of 4 or more lines: their line count is a multiple of 4).
-// FP64 single pass: element-wise copies (a complex128 element is itself a 16-byte vector)
-template <int LAY, int NT, bool LOAD>
-__device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, double2 *sm) {
-    const PassParams &p = a.p;
-    const int64_t lines = min((int64_t)a.C, p.total_lines - g0);
-    const int T = (int)lines * a.L;
-    const int64_t base = g0 * a.L;
-    const int cj = LOAD ? p.conj_in : p.conj_out;
-    const double *pin = reinterpret_cast<const double *>(p.in);
-    double *pout = reinterpret_cast<double *>(p.out);
-#pragma unroll 4
-    for (int f = threadIdx.x; f < T; f += NT) {
-        if constexpr (LOAD) {
-            double2 x;
-            if constexpr (LAY == LAYOUT_IL) {
-                x = __ldcs(reinterpret_cast<const double2 *>(pin) + base + f);
-            } else {
-                x.x = __ldcs(pin + base + f);
-                x.y = __ldcs(pin + p.in_plane + base + f);
-            }
-            if (cj) x.y = -x.y;
-            sm[f] = x;
-        } else {
-            double2 x = sm[f];
-            if (cj) x.y = -x.y;
-            if constexpr (LAY == LAYOUT_IL) {
-                __stcs(reinterpret_cast<double2 *>(pout) + base + f, x);
-            } else {
-                __stcs(pout + base + f, x.x);
-                __stcs(pout + p.out_plane + base + f, x.y);
-            }
-        }
-    }
-}
-
+// Single pass, FP32 split layout: the tile's lines are back to back in both planes, so the
+// first stage's input and the last stage's output move as flat 16-byte vectors per plane
+// through shared memory (pitch L) when the tile starts 16-byte aligned in both planes.
 template <int LAY, int NT, bool LOAD>
 __device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, float2 *sm) {
     const PassParams &p = a.p;
@@ -460,36 +487,62 @@ template <int KIND, int LIN, int LOUT, int NT, typename V>
 __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs a) {
     extern __shared__ __align__(16) unsigned char sm_mixed_raw[];
     V *sm_mixed = reinterpret_cast<V *>(sm_mixed_raw);
-    // the second buffer starts 16-byte aligned (the single-pass copies move 16-byte vectors)
     V *buf0 = sm_mixed, *buf1 = sm_mixed + ((a.C * a.pitch + 1) & ~1);
     const int64_t g0 = (int64_t)blockIdx.x * a.C;
-    if constexpr (KIND == KIND_ROWS) rows_copy<LIN, NT, true>(a, g0, buf0);
-    else mixed_load<KIND, LIN, NT>(a, g0, buf0);
-    __syncthreads();
-    V *src = buf0, *dst = buf1;
-    for (int s = 0; s < a.nst; ++s) {
-        switch (a.radix[s]) {
-            case 2: mixed_stage<2, NT>(a, s, src, dst); break;
-            case 3: mixed_stage<3, NT>(a, s, src, dst); break;
-            case 4: mixed_stage<4, NT>(a, s, src, dst); break;
-            case 5: mixed_stage<5, NT>(a, s, src, dst); break;
-            case 7: mixed_stage<7, NT>(a, s, src, dst); break;
-            case 6: mixed_stage<6, NT>(a, s, src, dst); break;
-            case 8: mixed_stage<8, NT>(a, s, src, dst); break;
-            case 9: mixed_stage<9, NT>(a, s, src, dst); break;
-            case 10: mixed_stage<10, NT>(a, s, src, dst); break;
-            case 12: mixed_stage<12, NT>(a, s, src, dst); break;
-            case 14: mixed_stage<14, NT>(a, s, src, dst); break;
-            case 15: mixed_stage<15, NT>(a, s, src, dst); break;
-            default: mixed_stage<16, NT>(a, s, src, dst); break;
+    if constexpr (KIND == KIND_ROWS) {
+        // single pass: the first stage reads HBM and the last writes it (lines back to back)
+        // (FP32 split with short lines: through shared memory with 16-byte vectors per plane,
+        // where the scalar 4-byte plane accesses of the direct stages cost more)
+        bool flat = false;
+        if constexpr (std::is_same<V, float2>::value && LIN == LAYOUT_SPLIT) flat = a.flat != 0;
+        if (flat) {
+            if constexpr (std::is_same<V, float2>::value && LIN == LAYOUT_SPLIT) rows_copy<LIN, NT, true>(a, g0, buf1);
+            __syncthreads();
+        } else if (a.nst == 1) {
+            run_stage<NT, V, 3, LIN, LOUT>(a, 0, nullptr, nullptr, g0);
+            return;
         }
+        V *src = buf0, *dst = buf1;
+        if (flat) run_stage<NT, V>(a, 0, buf1, buf0);
+        else run_stage<NT, V, 1, LIN, LOUT>(a, 0, nullptr, buf0, g0);
         __syncthreads();
-        V *t = src;
-        src = dst;
-        dst = t;
+        const int last = flat ? a.nst : a.nst - 1;
+        for (int s = 1; s < last; ++s) {
+            run_stage<NT, V>(a, s, src, dst);
+            __syncthreads();
+            V *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (flat) {
+            if constexpr (std::is_same<V, float2>::value && LIN == LAYOUT_SPLIT) rows_copy<LOUT, NT, false>(a, g0, src);
+        } else {
+            run_stage<NT, V, 2, LIN, LOUT>(a, a.nst - 1, src, nullptr, g0);
+        }
+    } else {
+        mixed_load<KIND, LIN, NT>(a, g0, buf0);
+        __syncthreads();
+        V *src = buf0, *dst = buf1;
+        for (int s = 0; s < a.nst; ++s) {
+            run_stage<NT, V>(a, s, src, dst);
+            __syncthreads();
+            V *t = src;
+            src = dst;
+            dst = t;
+        }
+        mixed_store<KIND, LOUT, NT>(a, g0, src);
     }
-    if constexpr (KIND == KIND_ROWS) rows_copy<LOUT, NT, false>(a, g0, src);
-    else mixed_store<KIND, LOUT, NT>(a, g0, src);
 }
+
+}  // namespace fftc
+
+namespace fftc {
+
+// kernel variants of one element type: [kind and layouts][CTA of 512 threads]
+typedef void (*MixedKernel)(MixedArgs);
+enum { MK_ROWS_IL, MK_ROWS_SPLIT, MK_COLS_IL, MK_COLS_SPLIT_IL, MK_COLS_SPLIT, MK_ROWST_IL, MK_ROWST_SPLIT, MK_COUNT };
+struct MixedKernelSet {
+    MixedKernel k[MK_COUNT][2];
+};
 
 }  // namespace fftc
