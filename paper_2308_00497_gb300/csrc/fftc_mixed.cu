@@ -20,7 +20,8 @@ static const int kMixedTile = 4096;        // FP32 elements per CTA tile for sho
 static const int kMixedSinglePass64 = 4096;  // the same for FP64 (16-byte elements)
 static const int kMixedTile64 = 2048;
 
-extern const MixedKernel kMixedRowsF32[2][2], kMixedRowsF64[2][2], kMixedStridedF32[5][2], kMixedStridedF64[5][2];
+extern const MixedKernel kMixedRowsF32[2][2], kMixedRowsF64[2][2], kMixedColsIlF32[2], kMixedColsIlF64[2],
+    kMixedColsSplitF32[2][2], kMixedColsSplitF64[2][2], kMixedRowsTF32[2][2], kMixedRowsTF64[2][2];
 
 struct MixedPass {
     MixedArgs args;
@@ -108,11 +109,12 @@ static bool check_div(const FastDiv &f, uint64_t limit) {
 static MixedKernel mixed_kernel(int kind, int lin, int lout, int nt, bool fp64) {
     const int w = nt == 512 ? 1 : 0;
     if (kind == KIND_ROWS) return (fp64 ? kMixedRowsF64 : kMixedRowsF32)[lin == LAYOUT_IL ? 0 : 1][w];
-    int v = -1;
-    if (kind == KIND_COLS) v = lin == LAYOUT_IL ? 0 : (lout == LAYOUT_IL ? 1 : 2);
-    else if (kind == KIND_ROWST) v = lout == LAYOUT_IL ? 3 : 4;
-    if (v < 0 || (kind == KIND_COLS && lin == LAYOUT_IL && lout != LAYOUT_IL)) return nullptr;
-    return (fp64 ? kMixedStridedF64 : kMixedStridedF32)[v][w];
+    if (kind == KIND_COLS) {
+        if (lin == LAYOUT_IL) return lout == LAYOUT_IL ? (fp64 ? kMixedColsIlF64 : kMixedColsIlF32)[w] : nullptr;
+        return (fp64 ? kMixedColsSplitF64 : kMixedColsSplitF32)[lout == LAYOUT_IL ? 0 : 1][w];
+    }
+    if (kind == KIND_ROWST && lin == LAYOUT_IL) return (fp64 ? kMixedRowsTF64 : kMixedRowsTF32)[lout == LAYOUT_IL ? 0 : 1][w];
+    return nullptr;
 }
 
 // stage tables of a line: stage s holds w_{Ns r}^{t k} at (t - 1) Ns + k (t < r, k < Ns)

@@ -217,36 +217,55 @@ __device__ __forceinline__ void dft_small(V *v) {
     }
 }
 
-// One stage over the tile. IO bit 0: the stage reads HBM (the single pass's first stage,
-// line g0 + c at element offset (g0 + c) L, coalesced over j), bit 1: it writes HBM (the
-// last stage, whose output index j + t Ns is coalesced over j); otherwise shared memory.
-template <int R, int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL>
+// One stage over the tile. IO bit 0: the stage reads HBM (the first stage), bit 1: it writes
+// HBM (the last stage); otherwise shared memory. Line g0 + c, element e sits at
+// (g / lpt) tr + (g mod lpt) line + e elem. CF: consecutive threads take consecutive lines
+// at one position (coalesced for column access: the four-step pass 1 reads and writes, and
+// pass 2's transposed writes); else consecutive positions of one line. KIND_COLS multiplies
+// its output by the inter-pass diagonal (when the plan has one).
+template <int R, int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL, int KIND = KIND_ROWS,
+          bool CF = false>
 __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *src, V *dst, int64_t g0 = 0) {
     using S = typename CplxT<V>::S;
+    const PassParams &p = a.p;
     const int L = a.L, Lr = L / R, Ns = a.ns[s];
     const int G = a.C * Lr;
-    const V *tw = reinterpret_cast<const V *>(a.p.tw) + a.tw_off[s];
+    const V *tw = reinterpret_cast<const V *>(p.tw) + a.tw_off[s];
 #pragma unroll 2
     for (int gi = threadIdx.x; gi < G; gi += NT) {
-        const int c = (int)fdiv((uint32_t)gi, a.div_lr[s]);
-        const int j = gi - c * Lr;
+        int c, j;
+        if constexpr (CF) {
+            j = (int)fdiv((uint32_t)gi, a.div_C);
+            c = gi - j * a.C;
+        } else {
+            c = (int)fdiv((uint32_t)gi, a.div_lr[s]);
+            j = gi - c * Lr;
+        }
         V v[R];
-        const bool live = !(IO & 3) || g0 + c < a.p.total_lines;
+        int64_t tr = 0, l = 0;
+        bool live = true;
+        if constexpr ((IO & 3) != 0) {
+            const int64_t g = g0 + c;
+            live = g < p.total_lines;
+            tr = fdiv((uint32_t)g, a.div_lpt);
+            l = g - tr * a.lpt;
+        }
         if constexpr (IO & 1) {
-            const int64_t b = (g0 + c) * L + j;
-            const S *pin = reinterpret_cast<const S *>(a.p.in);
+            const int64_t b = tr * p.in_tr + l * p.in_line + (int64_t)j * p.in_elem;
+            const S *pin = reinterpret_cast<const S *>(p.in);
 #pragma unroll
             for (int t = 0; t < R; ++t) {
                 V x = CplxT<V>::make(0, 0);
                 if (live) {
+                    const int64_t o = b + (int64_t)t * Lr * p.in_elem;
                     if constexpr (LIN == LAYOUT_IL) {
-                        x = __ldcs(reinterpret_cast<const V *>(pin) + b + t * Lr);
+                        x = __ldcs(reinterpret_cast<const V *>(pin) + o);
                     } else {
-                        x.x = __ldcs(pin + b + t * Lr);
-                        x.y = __ldcs(pin + a.p.in_plane + b + t * Lr);
+                        x.x = __ldcs(pin + o);
+                        x.y = __ldcs(pin + p.in_plane + o);
                     }
                 }
-                if (a.p.conj_in) x.y = -x.y;
+                if (p.conj_in) x.y = -x.y;
                 v[t] = x;
             }
         } else {
@@ -264,17 +283,24 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
         const int o = jq * Ns * R + jm;
         if constexpr (IO & 2) {
             if (live) {
-                const int64_t b = (g0 + c) * L + o;
-                S *pout = reinterpret_cast<S *>(a.p.out);
+                const int64_t b = tr * p.out_tr + l * p.out_line;
+                S *pout = reinterpret_cast<S *>(p.out);
 #pragma unroll
                 for (int t = 0; t < R; ++t) {
                     V x = v[t];
-                    if (a.p.conj_out) x.y = -x.y;
-                    if constexpr (LOUT == LAYOUT_IL) {
-                        __stcs(reinterpret_cast<V *>(pout) + b + t * Ns, x);
+                    const int e = o + t * Ns;
+                    if constexpr (KIND == KIND_COLS) {  // inter-pass diagonal: column l, row e
+                        if (p.tw2_full) x = cmul(x, __ldg(reinterpret_cast<const V *>(p.tw2_full) + (int64_t)e * a.lpt + l));
+                    }
+                    if (p.conj_out) x.y = -x.y;
+                    const int64_t q = b + (int64_t)e * p.out_elem;
+                    if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
+                        __stcg(reinterpret_cast<V *>(pout) + q, x);  // workspace: keep it in L2
+                    } else if constexpr (LOUT == LAYOUT_IL) {
+                        __stcs(reinterpret_cast<V *>(pout) + q, x);
                     } else {
-                        __stcs(pout + b + t * Ns, x.x);
-                        __stcs(pout + a.p.out_plane + b + t * Ns, x.y);
+                        __stcs(pout + q, x.x);
+                        __stcs(pout + p.out_plane + q, x.y);
                     }
                 }
             }
@@ -286,39 +312,23 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
     }
 }
 
-template <int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL>
+template <int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL, int KIND = KIND_ROWS,
+          bool CF = false>
 __device__ __forceinline__ void run_stage(const MixedArgs &a, int s, const V *src, V *dst, int64_t g0 = 0) {
     switch (a.radix[s]) {
-        case 2: mixed_stage<2, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 3: mixed_stage<3, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 4: mixed_stage<4, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 5: mixed_stage<5, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 6: mixed_stage<6, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 7: mixed_stage<7, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 8: mixed_stage<8, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 9: mixed_stage<9, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 10: mixed_stage<10, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 12: mixed_stage<12, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 14: mixed_stage<14, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        case 15: mixed_stage<15, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-        default: mixed_stage<16, NT, V, IO, LIN, LOUT>(a, s, src, dst, g0); break;
-    }
-}
-
-// Global <-> shared copies of a tile. Element a of tile line c is global line g0 + c,
-// at (g / lpt) * tr + (g mod lpt) * line_stride + a * elem_stride. Element-contiguous
-// lines are walked element-fastest, strided ones line-fastest (both coalesced).
-// a thread keeps kMixedBatch loads in flight before it writes any of them to shared memory
-constexpr int kMixedBatch = 16;
-
-template <int KIND>
-__device__ __forceinline__ void tile_coord(const MixedArgs &a, int f, int &c, int &e) {
-    if constexpr (KIND == KIND_COLS) {
-        e = (int)fdiv((uint32_t)f, a.div_C);
-        c = f - e * a.C;
-    } else {
-        c = (int)fdiv((uint32_t)f, a.div_L);
-        e = f - c * a.L;
+        case 2: mixed_stage<2, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 3: mixed_stage<3, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 4: mixed_stage<4, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 5: mixed_stage<5, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 6: mixed_stage<6, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 7: mixed_stage<7, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 8: mixed_stage<8, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 9: mixed_stage<9, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 10: mixed_stage<10, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 12: mixed_stage<12, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 14: mixed_stage<14, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        case 15: mixed_stage<15, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
+        default: mixed_stage<16, NT, V, IO, LIN, LOUT, KIND, CF>(a, s, src, dst, g0); break;
     }
 }
 
@@ -404,85 +414,6 @@ __device__ __forceinline__ void rows_copy(const MixedArgs &a, int64_t g0, float2
     }
 }
 
-template <int KIND, int LIN, int NT, typename V>
-__device__ __forceinline__ void mixed_load(const MixedArgs &a, int64_t g0, V *sm) {
-    using S = typename CplxT<V>::S;
-    const PassParams &p = a.p;
-    const int T = a.C * a.L;
-    const int cj = p.conj_in;
-    const S *pin = reinterpret_cast<const S *>(p.in);
-    for (int base = 0; base < T; base += NT * kMixedBatch) {
-        V x[kMixedBatch];
-#pragma unroll
-        for (int i = 0; i < kMixedBatch; ++i) {
-            const int f = base + i * NT + (int)threadIdx.x;
-            x[i] = CplxT<V>::make(0, 0);
-            int c, e;
-            tile_coord<KIND>(a, f, c, e);
-            const int64_t g = g0 + c;
-            if (f < T && g < p.total_lines) {
-                const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
-                const int64_t off = tr * p.in_tr + l * p.in_line + (int64_t)e * p.in_elem;
-                if constexpr (LIN == LAYOUT_IL) {
-                    x[i] = __ldcs(reinterpret_cast<const V *>(pin) + off);
-                } else {
-                    x[i].x = __ldcs(pin + off);
-                    x[i].y = __ldcs(pin + p.in_plane + off);
-                }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kMixedBatch; ++i) {
-            const int f = base + i * NT + (int)threadIdx.x;
-            if (f < T) {
-                int c, e;
-                tile_coord<KIND>(a, f, c, e);
-                if (cj) x[i].y = -x[i].y;
-                sm[c * a.pitch + e] = x[i];
-            }
-        }
-    }
-}
-
-template <int KIND, int LOUT, int NT, typename V>
-__device__ __forceinline__ void mixed_store(const MixedArgs &a, int64_t g0, const V *sm) {
-    using S = typename CplxT<V>::S;
-    const PassParams &p = a.p;
-    S *pout = reinterpret_cast<S *>(p.out);
-    const int L = a.L, C = a.C, T = C * L;
-    const int cj = p.conj_out;
-#pragma unroll 4
-    for (int f = threadIdx.x; f < T; f += NT) {
-        int c, e;
-        if constexpr (KIND == KIND_ROWS) {
-            c = (int)fdiv((uint32_t)f, a.div_L);
-            e = f - c * L;
-        } else {
-            e = (int)fdiv((uint32_t)f, a.div_C);
-            c = f - e * C;
-        }
-        const int64_t g = g0 + c;
-        if (g >= p.total_lines) continue;
-        const int64_t tr = fdiv((uint32_t)g, a.div_lpt), l = g - tr * a.lpt;
-        V x = sm[c * a.pitch + e];
-        if constexpr (KIND == KIND_COLS) {
-            // inter-pass diagonal of Eq. 1: column l, output row e: w_N^(l e) (four-step only;
-            // a strided axis of a multidimensional transform has none)
-            if (p.tw2_full) x = cmul(x, __ldg(reinterpret_cast<const V *>(p.tw2_full) + (int64_t)e * a.lpt + l));
-        }
-        if (cj) x.y = -x.y;
-        const int64_t off = tr * p.out_tr + l * p.out_line + (int64_t)e * p.out_elem;
-        if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
-            __stcg(reinterpret_cast<V *>(pout) + off, x);  // workspace: keep it in L2
-        } else if constexpr (LOUT == LAYOUT_IL) {
-            __stcs(reinterpret_cast<V *>(pout) + off, x);
-        } else {
-            __stcs(pout + off, x.x);
-            __stcs(pout + p.out_plane + off, x.y);
-        }
-    }
-}
-
 template <int KIND, int LIN, int LOUT, int NT, typename V>
 __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs a) {
     extern __shared__ __align__(16) unsigned char sm_mixed_raw[];
@@ -520,17 +451,24 @@ __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs 
             run_stage<NT, V, 2, LIN, LOUT>(a, a.nst - 1, src, nullptr, g0);
         }
     } else {
-        mixed_load<KIND, LIN, NT>(a, g0, buf0);
+        // four-step passes and strided axes: pass 1 (columns) reads and writes line-fastest;
+        // pass 2 reads its contiguous rows position-fastest and writes transposed line-fastest
+        constexpr bool CF_IN = KIND == KIND_COLS, CF_OUT = true;
+        if (a.nst == 1) {
+            run_stage<NT, V, 3, LIN, LOUT, KIND, CF_IN>(a, 0, nullptr, nullptr, g0);
+            return;
+        }
+        run_stage<NT, V, 1, LIN, LOUT, KIND, CF_IN>(a, 0, nullptr, buf0, g0);
         __syncthreads();
         V *src = buf0, *dst = buf1;
-        for (int s = 0; s < a.nst; ++s) {
+        for (int s = 1; s < a.nst - 1; ++s) {
             run_stage<NT, V>(a, s, src, dst);
             __syncthreads();
             V *t = src;
             src = dst;
             dst = t;
         }
-        mixed_store<KIND, LOUT, NT>(a, g0, src);
+        run_stage<NT, V, 2, LIN, LOUT, KIND, CF_OUT>(a, a.nst - 1, src, nullptr, g0);
     }
 }
 
