@@ -98,7 +98,7 @@ struct PipeRowsDefault {
     int logn, loge, lines, code;
 };
 static const PipeRowsDefault kPipeRowsDefaults[] = {
-    {9, 5, 8, 2}, {10, 5, 4, 2}, {11, 5, 2, 6}, {12, 4, 1, 5}, {13, 5, 1, 5}, {14, 5, 1, 5},
+    {9, 5, 8, 2}, {10, 5, 4, 2}, {11, 5, 2, 6}, {12, 5, 1, 5}, {13, 5, 1, 5}, {14, 5, 1, 5},
 };
 static const PipeRowsDefault *pipe_rows_default(int logn) {
     for (const PipeRowsDefault &d : kPipeRowsDefaults)

@@ -12,7 +12,7 @@ namespace fftc {
 
 extern const KernelEntry kPipeEarlyIlTable[] = {
     PRE(11, 5, 2, 2),     PRE(12, 4, 1, 1),     PRE(12, 4, 1, 2),     PRE(13, 5, 1, 1),     PRE(13, 5, 1, 2),
-    PRE(14, 5, 1, 1),
+    PRE(14, 5, 1, 1),     PRE(12, 5, 1, 1),
     PTE(8, 4, 16, 7, 2),  PTE(8, 4, 16, 8, 2),  PTE(9, 5, 8, 8, 2),   PTE(10, 5, 8, 8, 2),  PTE(10, 5, 8, 9, 2),
     PTE(10, 5, 8, 10, 2),
     PCE(7, 4, 16, 8, 1),  PCE(8, 4, 16, 8, 1),  PCE(8, 4, 16, 9, 1),  PCE(8, 4, 32, 10, 1), PCE(9, 4, 16, 10, 1),
