@@ -64,3 +64,16 @@ def test_dtype_dispatch_and_round_trip():
     y = fc.ifft(fc.fft(x))  # complex128 input selects the FP64 path
     assert y.dtype == torch.complex128
     assert torch.linalg.vector_norm(y - n * x) <= _tol(n) * n * torch.linalg.vector_norm(x)
+
+
+@pytest.mark.parametrize("n", [4096, 30000])
+def test_in_place_and_split_ragged(n):
+    import paper_2308_00497_gb300 as fc
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))
+    t = _to(x, "split")
+    fc.Plan(n, 3, "split", True, precision="fp64").execute(t, t)
+    torch.cuda.synchronize()
+    ref = oracle.fft(x, inverse=True)
+    y = _from(t, "split")
+    assert (np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() <= _tol(n)

@@ -98,3 +98,18 @@ def test_pointwise_is_refused_for_mixed_sizes():
     x = torch.zeros((2, 12), dtype=torch.complex64, device="cuda")
     with pytest.raises(RuntimeError):
         p.execute_pointwise(x, torch.ones(12, device="cuda"), 1.0)
+
+
+@pytest.mark.parametrize("n", [360, 100000])
+def test_in_place_batch_one_and_empty(n):
+    import paper_2308_00497_gb300 as fc
+    x = si.uniform_complex(1, n, seed=11)
+    t = to_device(x, "interleaved")
+    p = fc.Plan(n, 1)
+    p.execute(t, t)  # in place
+    torch.cuda.synchronize()
+    ref = oracle.fft(x.astype(np.complex128))
+    assert rel_l2_rows(t.cpu().numpy(), ref).max() <= tol_fp32(n)
+    e = fc.Plan(n, 0)
+    e.execute(torch.empty((0, n), dtype=torch.complex64, device="cuda"))
+    torch.cuda.synchronize()
