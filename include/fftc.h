@@ -115,7 +115,9 @@ fftc_status fftc_execute_host(fftc_plan plan, const void *host_in, void *host_ou
  * out[b][k] = scale * h[k] * X_b[k]: the plan's transforms with a real factor per output
  * frequency fused into the last pass (the diagonal step of a spectral filter, whose
  * adjoint is the same call on the opposite-direction plan). `h` is a device array of n
- * floats (16-byte aligned); the rest is as in fftc_execute. FFTC_FP32 plans only.
+ * floats (16-byte aligned); the rest is as in fftc_execute. FFTC_FP32 1D plans of any
+ * supported n (FFTC_ERR_INVALID_VALUE for tensor-core, FP64, uneven and multidimensional
+ * plans).
  */
 fftc_status fftc_execute_pointwise(fftc_plan plan, const void *in, void *out, const float *h, float scale,
                                    void *stream);

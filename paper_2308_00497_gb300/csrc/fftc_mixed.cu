@@ -291,14 +291,20 @@ static cudaError_t mixed_launch(const MixedPass &mp, const MixedArgs &a, cudaStr
                             (size_t)mp.smem, st);
 }
 
-fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st) {
+fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
+                      cudaStream_t st) {
     const MixedState *ms = p->mixed;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    if (post_h && p->precision != FFTC_FP32) return FFTC_ERR_INVALID_VALUE;
     if (ms->npasses == 1) {
         MixedArgs a = ms->pass[0].args;
         a.p.in = (const float *)in;
         a.p.out = (float *)out;
         a.p.conj_in = a.p.conj_out = inv;
+        a.p.post_h = post_h;
+        a.p.post_scale = post_scale;
+        a.p.post_line_mul = 0;  // frequency = position in the line
+        a.p.post_elem_mul = 1;
         return mixed_launch(ms->pass[0], a, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
     }
     MixedArgs a = ms->pass[0].args;
@@ -310,6 +316,10 @@ fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st
     b.p.in = (const float *)p->workspace;
     b.p.out = (float *)out;
     b.p.conj_out = inv;
+    b.p.post_h = post_h;  // pass 2 writes frequency k1 + M k2 (line k1, position k2)
+    b.p.post_scale = post_scale;
+    b.p.post_line_mul = 1;
+    b.p.post_elem_mul = ms->pass[0].args.L;
     return mixed_launch(ms->pass[1], b, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
 }
 

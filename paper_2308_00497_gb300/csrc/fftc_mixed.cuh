@@ -292,6 +292,12 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
                     if constexpr (KIND == KIND_COLS) {  // inter-pass diagonal: column l, row e
                         if (p.tw2_full) x = cmul(x, __ldg(reinterpret_cast<const V *>(p.tw2_full) + (int64_t)e * a.lpt + l));
                     }
+                    if (p.post_h) {  // the fused diagonal: frequency l * line_mul + e * elem_mul
+                        const S h = (S)(__ldg(p.post_h + l * p.post_line_mul + (int64_t)e * p.post_elem_mul) *
+                                        p.post_scale);
+                        x.x *= h;
+                        x.y *= h;
+                    }
                     if (p.conj_out) x.y = -x.y;
                     const int64_t q = b + (int64_t)e * p.out_elem;
                     if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
@@ -425,7 +431,8 @@ __global__ void __launch_bounds__(NT) k_mixed(const __grid_constant__ MixedArgs 
         // (FP32 split with short lines: through shared memory with 16-byte vectors per plane,
         // where the scalar 4-byte plane accesses of the direct stages cost more)
         bool flat = false;
-        if constexpr (std::is_same<V, float2>::value && LIN == LAYOUT_SPLIT) flat = a.flat != 0;
+        // (not with the fused diagonal, which the direct last stage applies)
+        if constexpr (std::is_same<V, float2>::value && LIN == LAYOUT_SPLIT) flat = a.flat != 0 && !a.p.post_h;
         if (flat) {
             if constexpr (std::is_same<V, float2>::value && LIN == LAYOUT_SPLIT) rows_copy<LIN, NT, true>(a, g0, buf1);
             __syncthreads();

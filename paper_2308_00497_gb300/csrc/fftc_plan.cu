@@ -335,9 +335,9 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     if (p->precision != FFTC_FP32 && post_h) return FFTC_ERR_INVALID_VALUE;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
     if (p->mixed || p->nd) {
-        if (post_h) return FFTC_ERR_INVALID_VALUE;
+        if (post_h && p->nd) return FFTC_ERR_INVALID_VALUE;
         if (ev) cudaEventRecord(ev[0], st);
-        fftc_status s = p->nd ? nd_run(p, in, out, st) : mixed_run(p, in, out, st);
+        fftc_status s = p->nd ? nd_run(p, in, out, st) : mixed_run(p, in, out, post_h, post_scale, st);
         if (ev) {
             cudaEventRecord(ev[1], st);
             cudaEventRecord(ev[2], st);

@@ -92,10 +92,25 @@ def test_plan_info_radices_multiply_to_n():
         assert got == passes and int(np.prod(radices)) == n and set(radices) <= {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16}
 
 
-def test_pointwise_is_refused_for_mixed_sizes():
+@pytest.mark.parametrize("n", [60, 3000, 12288])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_pointwise_diagonal(n, layout):
+    """out[k] = scale * h[k] * X[k] with the multiply fused into the last stage."""
     import paper_2308_00497_gb300 as fc
-    p = fc.Plan(12, 2)
-    x = torch.zeros((2, 12), dtype=torch.complex64, device="cuda")
+    B = 3
+    x = si.uniform_complex(B, n, seed=n + 3)
+    h = np.random.default_rng(n).uniform(0.5, 2.0, n).astype(np.float32)
+    p = fc.Plan(n, B, layout, False)
+    y = from_device(p.execute_pointwise(to_device(x, layout), torch.from_numpy(h).cuda(), 0.25), layout)
+    torch.cuda.synchronize()
+    ref = 0.25 * h.astype(np.float64) * oracle.fft(x.astype(np.complex128))
+    assert rel_l2_rows(y, ref).max() <= tol_fp32(n)
+
+
+def test_pointwise_is_refused_for_fp64():
+    import paper_2308_00497_gb300 as fc
+    p = fc.Plan(12, 2, precision="fp64")
+    x = torch.zeros((2, 12), dtype=torch.complex128, device="cuda")
     with pytest.raises(RuntimeError):
         p.execute_pointwise(x, torch.ones(12, device="cuda"), 1.0)
 
