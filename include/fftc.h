@@ -166,7 +166,8 @@ fftc_status fftc_plan_tune(fftc_plan plan, int reps);
  * Kronecker product of the 1D transforms, the (F (x) I)(I (x) F) form of Section 3 with
  * both factors whole DFTs: the last axis by a 1D plan (any length fftc_plan_create
  * accepts), every other axis by an in-place strided pass (length 2..8192 with prime
- * factors 2, 3, 5, 7). FFTC_FP32 only; at most 2^30 elements. Executed with
+ * factors 2, 3, 5, 7; up to 4096 for FFTC_FP64). FFTC_FP32 or FFTC_FP64 (complex128
+ * arrays); at most 2^30 elements. Executed with
  * fftc_execute (in place allowed); fftc_plan_info reports the HBM pass count and no
  * radices. Returns NULL on error (fftc_get_last_error tells why).
  */

@@ -170,28 +170,30 @@ class NdPlan(Plan):
     Interleaved tensors are complex64 [batch, *dims]; split tensors float32 [2, batch, *dims].
     """
 
-    def __init__(self, dims, batch: int, layout: str = "interleaved", inverse: bool = False, device=None):
+    def __init__(self, dims, batch: int, layout: str = "interleaved", inverse: bool = False, device=None,
+                 precision: str = "fp32"):
         import numpy as np
         lib = nat.load()
         self.dims = tuple(int(d) for d in dims)
         if len(self.dims) not in (2, 3):
             raise ValueError("dims must have 2 or 3 entries")
-        self.batch, self.layout, self.inverse, self.precision = int(batch), layout, bool(inverse), "fp32"
+        self.batch, self.layout, self.inverse, self.precision = int(batch), layout, bool(inverse), precision
         self.n = int(np.prod(self.dims))
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         d = np.ascontiguousarray(self.dims, dtype=np.int64)
         with torch.cuda.device(self.device):
             h = lib.fftc_plan_create_nd(len(self.dims), d.ctypes.data, self.batch, nat.LAYOUTS[layout],
-                                        nat.INVERSE if inverse else nat.FORWARD, nat.FP32)
+                                        nat.INVERSE if inverse else nat.FORWARD, nat.PRECISIONS[precision])
         if not h:
             raise nat.FftcError(lib.fftc_get_last_error(), f"fftc_plan_create_nd(dims={self.dims}, batch={batch})")
         self._h = ctypes.c_void_p(h)
 
     def _shape(self):
+        fp64 = self.precision == "fp64"
         if self.layout == "interleaved":
-            return (self.batch,) + self.dims, torch.complex64
-        return (2, self.batch) + self.dims, torch.float32
+            return (self.batch,) + self.dims, torch.complex128 if fp64 else torch.complex64
+        return (2, self.batch) + self.dims, torch.float64 if fp64 else torch.float32
 
 
 _cache: dict = {}
@@ -241,19 +243,21 @@ _nd_cache: dict = {}
 
 
 def _run_nd(x: torch.Tensor, rank: int, inverse: bool, layout: str, out=None) -> torch.Tensor:
+    precision = "fp64" if x.dtype in (torch.complex128, torch.float64) else "fp32"
+    cdt, rdt = (torch.complex128, torch.float64) if precision == "fp64" else (torch.complex64, torch.float32)
     if layout == "interleaved":
-        if x.dtype != torch.complex64 or x.dim() != rank + 1:
-            raise ValueError(f"interleaved input must be a complex64 [batch, {rank} dims] tensor")
+        if x.dtype != cdt or x.dim() != rank + 1:
+            raise ValueError(f"interleaved input must be a {cdt} [batch, {rank} dims] tensor")
         batch, dims = x.shape[0], tuple(x.shape[1:])
     else:
-        if x.dtype != torch.float32 or x.dim() != rank + 2 or x.shape[0] != 2:
-            raise ValueError(f"split input must be a float32 [2, batch, {rank} dims] tensor")
+        if x.dtype != rdt or x.dim() != rank + 2 or x.shape[0] != 2:
+            raise ValueError(f"split input must be a {rdt} [2, batch, {rank} dims] tensor")
         batch, dims = x.shape[1], tuple(x.shape[2:])
-    key = (dims, batch, layout, inverse, x.device.index)
+    key = (dims, batch, layout, inverse, precision, x.device.index)
     with _cache_lock:
         p = _nd_cache.get(key)
         if p is None:
-            p = _nd_cache[key] = NdPlan(dims, batch, layout, inverse, device=x.device)
+            p = _nd_cache[key] = NdPlan(dims, batch, layout, inverse, device=x.device, precision=precision)
     return p.execute(x.contiguous(), out)
 
 

@@ -285,12 +285,12 @@ fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc
     if (layout != FFTC_LAYOUT_INTERLEAVED && layout != FFTC_LAYOUT_SPLIT) return fail(FFTC_ERR_INVALID_VALUE);
     if (direction != FFTC_FORWARD && direction != FFTC_INVERSE) return fail(FFTC_ERR_INVALID_VALUE);
     if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_FP64) return fail(FFTC_ERR_INVALID_VALUE);
-    if (precision != FFTC_FP32) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    if (precision != FFTC_FP32 && precision != FFTC_FP64) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
     int64_t per = 1;
     for (int a = 0; a < rank; ++a) {
         const int64_t d = dims[a];
         const bool ok = a == rank - 1 ? (d >= 2 && d <= (int64_t(1) << 20) && (is_pow2(d) || mixed_supported(d)))
-                                      : nd_axis_supported(d);
+                                      : nd_axis_supported(d, precision == FFTC_FP64);
         if (!ok) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
         per *= d;
         if (per > (int64_t(1) << 30)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);

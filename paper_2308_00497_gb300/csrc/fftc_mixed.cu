@@ -353,7 +353,9 @@ static bool nd_fast_shape(int64_t L, int *logl, int *loge, int *lines) {
     return true;
 }
 
-bool nd_axis_supported(int64_t d) { return d >= 2 && d <= kMixedSinglePass && mixed_supported(d); }
+bool nd_axis_supported(int64_t d, bool fp64) {
+    return d >= 2 && d <= (fp64 ? kMixedSinglePass64 : kMixedSinglePass) && (mixed_supported(d) || (d & (d - 1)) == 0);
+}
 
 fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
     NdState *nd = new (std::nothrow) NdState();
@@ -390,7 +392,7 @@ fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
         const int64_t L = dims[a];
         const int ax = nd->naxes++;
         int logl = 0, loge = 0, lines = 0;
-        if (lay == LAYOUT_IL && (S & (S - 1)) == 0 && nd_fast_shape(L, &logl, &loge, &lines)) {
+        if (!is_fp64(p) && lay == LAYOUT_IL && (S & (S - 1)) == 0 && nd_fast_shape(L, &logl, &loge, &lines)) {
             const KernelEntry *k = find_kernel(KIND_COLS, logl, loge, lines, LAYOUT_IL, LAYOUT_IL, 0, 0);
             if (k) {
                 PassParams &q = nd->fastp[ax];
@@ -425,8 +427,9 @@ fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
         b.in_tr = b.out_tr = L * S;
         b.in_line = b.out_line = 1;
         b.in_elem = b.out_elem = S;
-        if (b.total_lines + mixed_lines(L) >= (int64_t(1) << 31)) return FFTC_ERR_UNSUPPORTED_SIZE;
-        st = mixed_pass_setup(p, mp, L, (int)std::min<int64_t>(S, mixed_lines(L)), KIND_COLS, lay, lay, S);
+        const bool fp64 = is_fp64(p);
+        if (b.total_lines + mixed_lines(L, fp64) >= (int64_t(1) << 31)) return FFTC_ERR_UNSUPPORTED_SIZE;
+        st = mixed_pass_setup(p, mp, L, (int)std::min<int64_t>(S, mixed_lines(L, fp64)), KIND_COLS, lay, lay, S);
         if (st != FFTC_OK) return st;
     }
     p->npasses = r->npasses + nd->naxes;

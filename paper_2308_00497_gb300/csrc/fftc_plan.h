@@ -101,7 +101,7 @@ void mixed_free(fftc_plan_s *p);
 fftc_status plan_tune(fftc_plan_s *p, int reps);
 
 // multidimensional transforms: a 1D plan along the last axis, strided passes along the others
-bool nd_axis_supported(int64_t d);
+bool nd_axis_supported(int64_t d, bool fp64);
 fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims);
 fftc_status nd_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t st);
 void nd_free(fftc_plan_s *p);

@@ -80,3 +80,19 @@ def test_separable_tone_closed_form():
     want = np.zeros((1,) + dims, complex)
     want[0, k[0], k[1]] = np.prod(dims)
     assert _rel(y, want).max() <= tol_fp32(int(np.prod(dims)))
+
+
+@pytest.mark.parametrize("dims", [(12, 100), (64, 64), (16, 8, 30)])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_fp64_arrays(dims, layout):
+    import math
+
+    import paper_2308_00497_gb300 as fc
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(N)
+    x = (rng.standard_normal((2,) + dims) + 1j * rng.standard_normal((2,) + dims))
+    t = (torch.from_numpy(np.ascontiguousarray(x)).cuda() if layout == "interleaved" else
+         torch.from_numpy(np.ascontiguousarray(np.stack([x.real, x.imag]))).cuda())
+    y = _from(fc.fftn(t, len(dims), layout=layout), layout)
+    ref = oracle.fftn(x, len(dims))
+    assert _rel(y, ref).max() <= 1e-14 * math.log2(N)
