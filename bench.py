@@ -343,7 +343,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = 0
         import oracle
-        rows = 24 * oracle.default_threads()
+        rows = 64 * oracle.default_threads()  # about 15 s of host work
         f, s, th = oracle_sample(rows)
         cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": th, "kind": "oracle",
                "sample": f"{rows} rows of each n=2^8..2^20 (forward, FP64); direct O(n^2) DFT for n<=4096, "
