@@ -335,7 +335,7 @@ struct NdState {
     fftc_plan_s *rows = nullptr;
     int naxes = 0;
     MixedPass axes[2];
-    // interleaved power-of-two axes of 64..1024 points: the compiled column pass
+    // power-of-two axes of 64..1024 points: the compiled column pass
     // (k_pass, runtime element stride) instead of the runtime-radix kernel
     const KernelEntry *fast[2] = {nullptr, nullptr};
     PassParams fastp[2];
@@ -392,13 +392,14 @@ fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
         const int64_t L = dims[a];
         const int ax = nd->naxes++;
         int logl = 0, loge = 0, lines = 0;
-        if (!is_fp64(p) && lay == LAYOUT_IL && (S & (S - 1)) == 0 && nd_fast_shape(L, &logl, &loge, &lines)) {
-            const KernelEntry *k = find_kernel(KIND_COLS, logl, loge, lines, LAYOUT_IL, LAYOUT_IL, 0, 0);
+        if (!is_fp64(p) && (S & (S - 1)) == 0 && nd_fast_shape(L, &logl, &loge, &lines)) {
+            const KernelEntry *k = find_kernel(KIND_COLS, logl, loge, lines, lay, lay, 0, 0);
             if (k) {
                 PassParams &q = nd->fastp[ax];
                 memset(&q, 0, sizeof(q));
                 q.err = p->d_err;
                 q.total_lines = outer * S;
+                q.in_plane = q.out_plane = plane;
                 int ls = 0;
                 while ((int64_t(1) << ls) < S) ++ls;
                 q.log_lpt = ls;

@@ -165,7 +165,7 @@ struct Pass {
                     x.y *= h;
                 }
                 if (cj) x.y = -x.y;
-                if constexpr (KIND == KIND_COLS) {
+                if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
                     __stcg(p2 + off, x);  // workspace: keep it in L2 for pass 2
                 } else if constexpr (LOUT == LAYOUT_IL) {
                     __stcs(p2 + off, x);

@@ -4,9 +4,10 @@
 namespace fftc {
 
 extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
-    kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[];
+    kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[],
+    kColsSplitTable[];
 extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count,
-    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount;
+    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount, kColsSplitCount;
 
 struct TableRef {
     const KernelEntry *t;
@@ -18,6 +19,7 @@ static const TableRef kTables[] = {
     {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
     {kPipeRowsIlTable, &kPipeRowsIlCount}, {kPipeRowsSplitTable, &kPipeRowsSplitCount}, {kPipe4Table, &kPipe4Count},
     {kPipeEarlyIlTable, &kPipeEarlyIlCount}, {kPipeEarlySplitTable, &kPipeEarlySplitCount},
+    {kColsSplitTable, &kColsSplitCount},
 };
 
 int kernel_count() {
