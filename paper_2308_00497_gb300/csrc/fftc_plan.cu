@@ -1,4 +1,5 @@
-// Planner and executor of the FP32 Stockham path.
+// Planner and executor of the FP32 power-of-two Stockham path (other lengths, FP64 and
+// multidimensional plans are built in fftc_mixed.cu; plan_run dispatches to them).
 //
 // n <= 2^14: one fused pass (KIND_ROWS), each CTA transforming whole rows.
 // n >  2^14: Eq. 1 applied once at the HBM level, n = M * K (four-step):
