@@ -445,6 +445,7 @@ def run_extras(args, dev) -> dict:
                               "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
     del xs, ts, xf
     out["mixed_radix"] = run_mixed(dev, reps)
+    out["large_n"] = run_large(dev, reps)
     out["multidim"] = run_nd(dev, reps)
     out["fp64"] = run_fp64(dev, reps)
     if not args.no_precision:
@@ -531,6 +532,37 @@ def run_mixed(dev, reps: int) -> dict:
                         "hbm_frac_strict": round(16.0 * n * B / (t * 1e-3) / 1e9 / peaks()[0], 4)})
     return {"workload": "mixed-radix n (factors 2, 3, 5, 7), n*batch ~ 2^26, forward, interleaved + split",
             "results": res}
+
+
+LARGE_SIZES = [1 << 21, 1 << 22, 1 << 23, 1 << 24, 3 ** 15]
+
+
+def run_large(dev, reps: int) -> dict:
+    """Lengths above the sweep, n = 2^21..2^24 (both layouts) and 3^15 (interleaved), batch =
+    2^26 // n, forward: ms, GFLOP/s (5 n log2 n), and the HBM fraction strict (16 B per
+    element) and per pass (16 B per element and pass)."""
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    res = []
+    xbuf = torch.randn(2 * ELEMS, device=dev)
+    ybuf = torch.empty_like(xbuf)
+    for n in LARGE_SIZES:
+        B = max(1, ELEMS // n)
+        for layout in (LAYOUTS if n & (n - 1) == 0 else ["interleaved"]):
+            if layout == "interleaved":
+                x = xbuf[:2 * n * B].view(torch.complex64).view(B, n)
+                y = ybuf[:2 * n * B].view(torch.complex64).view(B, n)
+            else:
+                x, y = xbuf[:2 * n * B].view(2, B, n), ybuf[:2 * n * B].view(2, B, n)
+            p = fc.Plan(n, B, layout, False, device=dev)
+            t = _time_ms(lambda: p.execute(x, y), reps)
+            frac = 16.0 * n * B / (t * 1e-3) / 1e9 / peaks()[0]
+            res.append({"n": n, "batch": B, "layout": layout, "passes": p.info()[0], "ms": round(t, 4),
+                        "gflops": round(flops(n, B) / (t * 1e-3) / 1e9, 1), "hbm_frac_strict": round(frac, 4),
+                        "hbm_frac_per_pass": round(frac * p.info()[0], 4)})
+            del p
+    return {"workload": "n = 2^21..2^24 and 3^15, n*batch ~ 2^26, forward", "results": res}
 
 
 def run_precision(args, dev, reps: int) -> dict:

@@ -65,9 +65,10 @@ typedef enum {
 typedef enum {
     FFTC_OK = 0,
     FFTC_ERR_INVALID_VALUE = 1,   /* a NULL pointer, a bad enum, a negative count */
-    FFTC_ERR_UNSUPPORTED_SIZE = 2,/* n outside [2, 2^20] or with a prime factor above 7, a
-                                     non-power-of-two n with a tensor-core precision, or
-                                     batch too large */
+    FFTC_ERR_UNSUPPORTED_SIZE = 2,/* n outside [2, 2^24] or with a prime factor above 7, a
+                                     non-power-of-two n with a tensor-core precision, an
+                                     FP64 n above 4096 with no split M K into factors of
+                                     at most 4096, or batch too large */
     FFTC_ERR_MISALIGNED = 3,      /* a data pointer not 16-byte aligned */
     FFTC_ERR_ALLOC = 4,           /* device or host allocation failed in plan creation */
     FFTC_ERR_CUDA = 5,            /* a CUDA runtime call or kernel launch failed */
@@ -76,16 +77,18 @@ typedef enum {
 } fftc_status;
 
 /*
- * Create a plan for `batch` transforms of length n, 2 <= n <= 2^20, in the given
+ * Create a plan for `batch` transforms of length n, 2 <= n <= 2^24, in the given
  * layout, direction and precision, on the current CUDA device. n is a power of two,
  * or (FFTC_FP32 only) any n = 2^a 3^b 5^c 7^d: Eq. 1 with mixed radices 16, 8, 4, 2,
  * 7, 5 and 3 (the mixed radix the paper names as missing, Sections 4 and 6), one
- * pass up to n = 8192 and two passes (n = M K) above.
+ * pass up to n = 8192 and two passes (n = M K) above. Powers of two take one pass up
+ * to 2^14 and two above (Eq. 1 once at the memory level, factors up to 2^12).
  * Precomputes the twiddle diagonals D (Eq. 1; Table 1 "Mul") in FP64 with exact
  * integer angle reduction and rounds them once to the working precision.
  * Returns NULL on error; fftc_get_last_error() then tells why.
  * Tensor-core precisions require a power of two n >= 16. FFTC_FP64 takes any n the
- * FP32 path takes (one pass up to 4096, two above); its buffers hold complex128.
+ * FP32 path takes (one pass up to 4096, two above, both factors at most 4096); its
+ * buffers hold complex128.
  */
 fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_direction direction,
                            fftc_precision precision);

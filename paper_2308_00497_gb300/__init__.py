@@ -1,5 +1,5 @@
 """GB300 batched complex-to-complex FFT (fused Stockham kernels for sm_103a): 1D of any
-length 2..2^20 with prime factors 2, 3, 5, 7, and rank-2/3 arrays.
+length 2..2^24 with prime factors 2, 3, 5, 7, and rank-2/3 arrays.
 
 The transforms run in libfftc.so (C ABI: include/fftc.h); this package is its
 thin Python binding, with torch supplying device memory and streams.

@@ -200,9 +200,13 @@ fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_di
     if (direction != FFTC_FORWARD && direction != FFTC_INVERSE) return fail(FFTC_ERR_INVALID_VALUE);
     if ((int)precision < (int)FFTC_FP32 || (int)precision > (int)FFTC_FP64) return fail(FFTC_ERR_INVALID_VALUE);
     if (batch < 0) return fail(FFTC_ERR_INVALID_VALUE);
-    if (n < 2 || n > (int64_t(1) << 20)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    if (n < 2 || n > (int64_t(1) << 24)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
     const bool tc = precision != FFTC_FP32 && precision != FFTC_FP64;
     if (!is_pow2(n) && (!mixed_supported(n) || tc)) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
+    // FP64 and non-power-of-two lengths run the runtime-radix path: it needs n = M K with
+    // both factors at most one CTA's line
+    if ((!is_pow2(n) || precision == FFTC_FP64) && mixed_split(n, precision == FFTC_FP64) == 0)
+        return fail(FFTC_ERR_UNSUPPORTED_SIZE);
     if (batch > (int64_t(1) << 40) / n) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
 
     fftc_plan_s *p = new (std::nothrow) fftc_plan_s();
@@ -289,7 +293,7 @@ fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc
     int64_t per = 1;
     for (int a = 0; a < rank; ++a) {
         const int64_t d = dims[a];
-        const bool ok = a == rank - 1 ? (d >= 2 && d <= (int64_t(1) << 20) && (is_pow2(d) || mixed_supported(d)))
+        const bool ok = a == rank - 1 ? (d >= 2 && d <= (int64_t(1) << 24) && (is_pow2(d) || mixed_supported(d)))
                                       : nd_axis_supported(d, precision == FFTC_FP64);
         if (!ok) return fail(FFTC_ERR_UNSUPPORTED_SIZE);
         per *= d;

@@ -38,11 +38,24 @@ struct MixedState {
 };
 
 bool mixed_supported(int64_t n) {
-    if (n < 2 || n > (int64_t(1) << 20)) return false;
+    if (n < 2 || n > (int64_t(1) << 24)) return false;
     int64_t m = n;
     for (int p : {2, 3, 5, 7})
         while (m % p == 0) m /= p;
     return m == 1;
+}
+
+// The first factor M of the split n = M K used above one CTA's line (M closest to sqrt n
+// with both factors at most that line), 0 when n has none, n itself for one pass.
+int64_t mixed_split(int64_t n, bool fp64) {
+    const int64_t single = fp64 ? kMixedSinglePass64 : kMixedSinglePass;
+    if (n <= single) return n;
+    int64_t M = 0;
+    for (int64_t m = 2; m <= single; ++m)
+        if (n % m == 0 && n / m <= single &&
+            (M == 0 || std::llabs((long long)(m * m - n)) < std::llabs((long long)(M * M - n))))
+            M = m;
+    return M;
 }
 
 // Radices of a line in stage order, at most 16 (a butterfly's values stay in registers):
@@ -225,11 +238,7 @@ fftc_status mixed_build(fftc_plan_s *p) {
         return mixed_pass_setup(p, mp, n, C >= 4 ? C / 4 * 4 : C, KIND_ROWS, lay, lay, 1);
     }
     // n = M K with both factors at most one CTA's line, M as close to sqrt(n) as possible
-    int64_t M = 0;
-    for (int64_t m = 2; m <= single; ++m)
-        if (n % m == 0 && n / m <= single &&
-            (M == 0 || std::llabs((long long)(m * m - n)) < std::llabs((long long)(M * M - n))))
-            M = m;
+    const int64_t M = mixed_split(n, fp64);
     if (M == 0) return FFTC_ERR_UNSUPPORTED_SIZE;
     const int64_t K = n / M;
     ms->npasses = p->npasses = 2;

@@ -64,6 +64,11 @@ static const FourStepDefault kFourStepDefaults[] = {
     {14, 7, 4, 16, 0, 0, 1, 4, 16, 0}, {15, 7, 4, 16, 0, 5, 1, 4, 16, 0}, {16, 8, 4, 16, 0, 5, 1, 4, 16, 0},
     {17, 8, 4, 16, 0, 5, 1, 5, 8, 6},  {18, 8, 4, 32, 5, 5, 1, 5, 8, 6},  {19, 9, 4, 16, 0, 5, 1, 5, 8, 6},
     {20, 10, 5, 8, 0, 0, 0, 5, 8, 6},
+    // above 2^20 a factor exceeds 2^10: column tiles of 16 lines of 2^10, 8 of 2^11 or 4 of
+    // 2^12 with 16 elements per thread (1024 threads); pass 2 fed by one bulk copy per tile
+    // except at 2^24 (the best of both layouts together)
+    {21, 10, 4, 16, 0, 0, 0, 5, 8, 5}, {22, 11, 4, 8, 0, 0, 0, 5, 8, 5},  {23, 12, 4, 4, 0, 0, 0, 5, 8, 5},
+    {24, 12, 4, 4, 0, 0, 0, 4, 4, 0},
 };
 
 FourStepChoice choose_four_step(int logn, int lay) {
@@ -78,8 +83,8 @@ FourStepChoice choose_four_step(int logn, int lay) {
     c.e2 = env_int("FFTC_TUNE_ROWST_E", same ? d->e2 : (k >= 9 ? 5 : 4));
     if (c.e1 > m) c.e1 = m;
     if (c.e2 >= k) c.e2 = k - 1;
-    c.c1 = env_int("FFTC_TUNE_COLS_C", same ? d->c1 : (m >= 10 ? 8 : 16));
-    c.c2 = env_int("FFTC_TUNE_ROWST_C", same ? d->c2 : (k >= 9 ? 8 : 16));
+    c.c1 = env_int("FFTC_TUNE_COLS_C", same ? d->c1 : (m >= 12 ? 4 : (m >= 10 ? 8 : 16)));
+    c.c2 = env_int("FFTC_TUNE_ROWST_C", same ? d->c2 : (k >= 12 ? 4 : (k >= 9 ? 8 : 16)));
     c.p1 = same ? (lay == LAYOUT_SPLIT ? d->p1_split : d->p1_il) : 0;
     c.p2 = same ? d->p2 : 0;
     c.pf = env_int("FFTC_PF", same ? d->pf : 0);
@@ -228,8 +233,10 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     p->tw2_lo = (float2 *)d;
     if (plan_upload(p, hi.data(), hi.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     p->tw2_hi = (float2 *)d;
-    // the whole diagonal D^n_M of Eq. 1 in pass-1 layout: entry t' * K + b = w_n^(b t')
-    {
+    // the whole diagonal D^n_M of Eq. 1 in pass-1 layout: entry t' * K + b = w_n^(b t');
+    // above 2^20 points (8 MB) pass 1 takes the product of the two small tables instead,
+    // which stay in L1 and L2 where a table of n entries would not
+    if (p->logn <= 20) {
         std::vector<float2> full((size_t)n);
         for (int64_t tp = 0; tp < M; ++tp)
             for (int64_t b = 0; b < K; ++b) {
@@ -253,6 +260,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         // tensor-map fed pass where it measured faster (narrow column boxes make the
         // bulk-copy engine issue one small request per row, so plain loads often win)
         if (p1code) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk, p1code);
+        if (p1code && !pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0, p1code);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;
@@ -288,6 +296,7 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pp.lout = lay;
         pp.k = nullptr;
         if (p2code) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm, p2code);
+        if (p2code && !pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0, p2code);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
         PassParams &b = pp.base;

@@ -90,6 +90,7 @@ int uneven_max_logn(const fftc_plan_s *p);
 
 // mixed radix, n = 2^a 3^b 5^c 7^d not a power of two (fftc_mixed.cu)
 bool mixed_supported(int64_t n);
+int64_t mixed_split(int64_t n, bool fp64);
 fftc_status mixed_build(fftc_plan_s *p);
 fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
                       cudaStream_t st);

@@ -5,9 +5,9 @@ namespace fftc {
 
 extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
     kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[],
-    kColsSplitTable[];
+    kColsSplitTable[], kLargeTable[], kPipeLargeTable[];
 extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count,
-    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount, kColsSplitCount;
+    kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount, kColsSplitCount, kLargeCount, kPipeLargeCount;
 
 struct TableRef {
     const KernelEntry *t;
@@ -19,7 +19,8 @@ static const TableRef kTables[] = {
     {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
     {kPipeRowsIlTable, &kPipeRowsIlCount}, {kPipeRowsSplitTable, &kPipeRowsSplitCount}, {kPipe4Table, &kPipe4Count},
     {kPipeEarlyIlTable, &kPipeEarlyIlCount}, {kPipeEarlySplitTable, &kPipeEarlySplitCount},
-    {kColsSplitTable, &kColsSplitCount},
+    {kColsSplitTable, &kColsSplitCount}, {kLargeTable, &kLargeCount},
+    {kPipeLargeTable, &kPipeLargeCount},
 };
 
 int kernel_count() {

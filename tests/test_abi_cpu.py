@@ -43,11 +43,26 @@ def test_status_strings(lib):
     assert nat.status_string(99) == "FFTC_ERR_UNKNOWN"
 
 
-@pytest.mark.parametrize("n", [0, 1, 11, 22, 143, 1 << 21, 3 << 19, -8])
+@pytest.mark.parametrize("n", [0, 1, 11, 22, 143, 1 << 25, 3 << 23, 7 * (1 << 22), -8])
 def test_unsupported_sizes_rejected_before_any_device_call(lib, n):
-    """Lengths outside [2, 2^20] or with a prime factor above 7."""
+    """Lengths outside [2, 2^24] or with a prime factor above 7."""
     from paper_2308_00497_gb300 import _native as nat
     assert not lib.fftc_plan_create(n, 4, 0, -1, 0)
+    assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
+
+
+def _splits(n, line):
+    return n <= line or any(n % m == 0 and n // m <= line for m in range(2, line + 1))
+
+
+@pytest.mark.parametrize("n", [9565938, 12907776])
+def test_fp64_lengths_without_a_two_factor_split_rejected(lib, n):
+    """FP64 runs lines of at most 4096 points: above that n needs n = M K with M, K <= 4096.
+    These 7-smooth lengths below 2^24 have none (a brute-force divisor search says so),
+    while FP32 lines of 8192 split them."""
+    from paper_2308_00497_gb300 import _native as nat
+    assert not _splits(n, 4096) and _splits(n, 8192)
+    assert not lib.fftc_plan_create(n, 4, 0, -1, nat.FP64)
     assert lib.fftc_get_last_error() == nat.ERR_UNSUPPORTED_SIZE
 
 
@@ -99,7 +114,7 @@ def test_uneven_validation_before_any_device_call(lib):
     assert lib.fftc_get_last_error() == nat.ERR_INVALID_VALUE          # split layout
 
 
-@pytest.mark.parametrize("dims", [(16384, 4), (11, 16), (4, 22), (1, 8), (8, 1 << 21)])
+@pytest.mark.parametrize("dims", [(16384, 4), (11, 16), (4, 22), (1, 8), (8, 1 << 25)])
 def test_nd_unsupported_shapes_rejected_before_any_device_call(lib, dims):
     import ctypes
     from paper_2308_00497_gb300 import _native as nat
