@@ -111,6 +111,22 @@ def test_large_n_radix2_tone_and_parseval():
     np.testing.assert_allclose(np.sum(np.abs(R) ** 2, axis=1), n * np.sum(np.abs(r) ** 2, axis=1), rtol=1e-12)
 
 
+def test_radix2_at_2p24_tone_and_numpy():
+    """The sizes the oracle checks the 2^21..2^24 kernels at: a tone at 2^24 in closed form,
+    and numpy's FFT on a random row at 2^22 (its own code, not this oracle's)."""
+    n = 1 << 24
+    j = np.arange(n, dtype=np.int64)
+    k0 = 9876543
+    x = np.exp(2j * np.pi * ((k0 * j) % n) / n)
+    X = oracle.fft_r2(x[None, :])[0]
+    assert abs(X[k0] - n) < 1e-13 * n
+    X[k0] = 0.0
+    assert np.abs(X).max() < 1e-13 * n
+    del x, X
+    r = si.uniform_complex(1, 1 << 22, seed=22).astype(np.complex128)
+    assert _rel(oracle.fft_r2(r), np.fft.fft(r, axis=1)) < 1e-13
+
+
 @pytest.mark.parametrize("name,f", ROUTINES)
 def test_linearity_parseval_roundtrip(name, f):
     n = 256
