@@ -317,6 +317,15 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
     bytes_per_launch = 16.0 * ELEMS
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / (dom_avg_ms * 1e-3) / 1e9
+    # every kernel kind's own fraction, and the whole timed step's: strict (16 B per element
+    # and transform, whatever the pass count) and per pass (16 B per element and HBM pass)
+    per_kind = {k: round(bytes_per_launch / (v["ms"] / v["launches"] * 1e-3) / 1e9 / peak, 4)
+                for k, v in kinds.items() if v["launches"]}
+    step_ms = ms / args.steps
+    step_passes = sum(p.info()[0] for *_, p in plans)
+    sweep = {"strict_frac": round(bytes_per_launch * len(plans) / (step_ms * 1e-3) / 1e9 / peak, 4),
+             "per_pass_frac": round(bytes_per_launch * step_passes / (step_ms * 1e-3) / 1e9 / peak, 4),
+             "transforms_per_step": len(plans), "hbm_passes_per_step": step_passes}
     step_flops = sum(flops(1 << e, ELEMS // (1 << e)) for e, *_ in plans)
     value = weak_scaling_value(world, step_flops, args.steps, ms)
 
@@ -364,7 +373,8 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": stored_traffic(dom), "bytes_per_launch": bytes_per_launch,
-                         "avg_launch_ms": round(dom_avg_ms, 5), "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()}},
+                         "avg_launch_ms": round(dom_avg_ms, 5), "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()},
+                         "per_kind_frac": per_kind, "sweep": sweep},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
@@ -440,12 +450,25 @@ def run_extras(args, dev) -> dict:
         yv.backward(2.0 * (yv.detach() - ts))   # dL/dy of ||y - t||^2
     t_fb = _time_ms(fwd_bwd, reps)
     fp = fc.get_plan(nn, B, "interleaved", False, device=dev)
+    ip = fc.get_plan(nn, B, "interleaved", True, device=dev)
     xf = xs.detach().clone()
     t_fft = _time_ms(lambda: fp.execute(xf, xf), reps)
+    # the library's share of the step: the same four launches (forward with the filter fused,
+    # inverse, twice) on preallocated buffers; the rest is torch (autograd, the 2(y - t)
+    # elementwise ops, allocations)
+    uf, gf = torch.empty_like(xf), torch.empty_like(xf)
+    def lib_only():
+        fp.execute_pointwise(xf, H, 1.0 / nn, out=uf)
+        ip.execute(uf, uf)
+        fp.execute_pointwise(uf, H, 1.0 / nn, out=gf)
+        ip.execute(gf, gf)
+    t_lib = _time_ms(lib_only, reps)
     out["spectral_filter"] = {"workload": "y = ifft(H * fft(x)) / n, loss ||y - t||^2, x,t [1024, 2^14] complex64",
                               "fwd_bwd_ms": round(t_fb, 4), "fft_ms": round(t_fft, 4),
+                              "library_ms": round(t_lib, 4), "torch_ms": round(max(t_fb - t_lib, 0.0), 4),
+                              "library_over_4_ffts": round(t_lib / (4 * t_fft), 3),
                               "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
-    del xs, ts, xf
+    del xs, ts, xf, uf, gf
     out["mixed_radix"] = run_mixed(dev, reps)
     out["large_n"] = run_large(dev, reps)
     out["multidim"] = run_nd(dev, reps)

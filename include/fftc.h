@@ -129,13 +129,20 @@ fftc_status fftc_execute_pointwise(fftc_plan plan, const void *in, void *out, co
  * complex element); 0 for an invalid plan. */
 int64_t fftc_plan_bytes(fftc_plan plan);
 
-/* Release the plan and its device memory. NULL is a no-op returning FFTC_OK. */
+/* Release the plan and its device memory: the end of the plan life cycle of the
+ * FFTW-like library interface the paper's generated code is called through (Section 4:
+ * a static library with a plan / execute / destroy style API). NULL is a no-op
+ * returning FFTC_OK; a destroyed or foreign handle returns FFTC_ERR_INVALID_PLAN. */
 fftc_status fftc_destroy(fftc_plan plan);
 
-/* Status of the last fftc_plan_create* call on this host thread. */
+/* Status of the last fftc_plan_create* call on this host thread (plan creation returns
+ * NULL on failure, as the planner calls of the FFTW-like interface of Section 4 do; this
+ * call says why). Thread-local; never fails. */
 fftc_status fftc_get_last_error(void);
 
-/* Static, human-readable name of a status code. */
+/* Static, human-readable name of a status code (the error reporting of the library
+ * interface of Section 4 is status codes only). Unknown codes map to a fixed string;
+ * the result is never NULL and must not be freed. */
 const char *fftc_status_string(fftc_status s);
 
 /*
@@ -240,7 +247,11 @@ fftc_status fftc_plan_pass_times(fftc_plan plan, double *ms_per_pass, int *execu
  * Calls no cudaMalloc, cudaFree or other allocating routine. The first call on a device
  * sets that device up (looks up the arrays' device addresses with the device current,
  * uploads the tables with a synchronous copy); make that first call before any stream
- * capture. Every call on a device shares the one scratch array, which keeps the last
+ * capture. With CUDA's lazy module loading the arrays' storage is committed on that
+ * first call, not when the library is loaded: make it at start-up, before a caching
+ * allocator has reserved the device's memory; if the device has no room left it returns
+ * FFTC_ERR_ALLOC. Later calls look the scratch address up again and repeat the set-up
+ * when it has changed (after cudaDeviceReset the module, and so its arrays, are new). Every call on a device shares the one scratch array, which keeps the last
  * call's contents (no call relies on it starting at zero: pass 1 overwrites every element
  * that pass 2 reads), so calls that can overlap on the GPU (different streams, or a
  * plan-free call racing another) corrupt each other's results: serialise them.

@@ -5,7 +5,9 @@ budget, a loop that forbids allocation after start-up).
 Called through the C ABI, its output must match the plan-based entry point
 (fftc_execute) on the same input within the FP32 tolerance of the other tests,
 on two calls in a row (the second one reuses the shared scratch array, which
-then holds the first call's data). This file is collected last on purpose.
+then holds the first call's data), and sampled rows must match the FP64 oracle
+within the same tolerance, so that the result stands on its own and not only
+against the library's other path. This file is collected last on purpose.
 """
 import ctypes
 
@@ -13,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synthetic_inputs as si
 from gpu_util import from_device, rel_l2_rows, to_device, tol_fp32
 
@@ -28,18 +31,23 @@ def lib():
 
 @pytest.mark.parametrize("e,batch,layout,inverse", [
     (14, 64, "interleaved", False),
+    (15, 8, "split", False),
     (16, 32, "split", True),
-    (20, 2, "interleaved", True),
     (17, 3, "split", False),
+    (18, 8, "interleaved", True),
+    (19, 4, "split", True),
+    (20, 2, "interleaved", True),
 ])
-def test_noalloc_matches_plan_two_calls(lib, e, batch, layout, inverse):
+def test_noalloc_matches_plan_and_oracle_two_calls(lib, e, batch, layout, inverse):
     from paper_2308_00497_gb300 import _native as nat
     import paper_2308_00497_gb300 as fc
     n = 1 << e
     plan = fc.Plan(n, batch, layout, inverse)
     stream = torch.cuda.current_stream().cuda_stream
+    rows = sorted({0, batch - 1})
     for call, seed in enumerate((11, 12)):  # two calls in a row, different data
-        x = to_device(si.uniform_complex(batch, n, seed=seed + e), layout)
+        xh = si.uniform_complex(batch, n, seed=seed + e)
+        x = to_device(xh, layout)
         ref = plan.execute(x)
         out = torch.empty_like(x)
         st = lib.fftc_execute_noalloc(n, batch, nat.LAYOUTS[layout], nat.INVERSE if inverse else nat.FORWARD,
@@ -47,8 +55,12 @@ def test_noalloc_matches_plan_two_calls(lib, e, batch, layout, inverse):
                                       ctypes.c_void_p(stream))
         assert st == nat.OK, nat.status_string(st)
         torch.cuda.synchronize()
-        err = rel_l2_rows(from_device(out, layout), from_device(ref, layout).astype(np.complex128))
+        got = from_device(out, layout)
+        err = rel_l2_rows(got, from_device(ref, layout).astype(np.complex128))
         assert err.max() <= tol_fp32(n), (call, float(err.max()))
+        want = oracle.fft(xh[rows].astype(np.complex128), inverse=inverse)
+        err_o = rel_l2_rows(got[rows], want)
+        assert err_o.max() <= tol_fp32(n), (call, float(err_o.max()))
 
 
 def test_noalloc_rejects_out_of_range(lib):
