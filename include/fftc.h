@@ -154,17 +154,30 @@ const char *fftc_status_string(fftc_status s);
 fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_radices);
 
 /*
+ * The split of a 1D plan into HBM passes: *m and *k with m * k = n, m the length of the
+ * pass-1 column transforms and k of the pass-2 row transforms of the four-step form
+ * (Eq. 1 applied once at the memory level, N = M K). A one-pass plan reports m = n, k = 1.
+ * Either pointer may be NULL. FFTC_ERR_INVALID_VALUE for uneven and multidimensional plans.
+ */
+fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k);
+
+/*
  * Measure-mode planning (the runtime search over decompositions that the paper leaves
  * to future work, Section 6; FFTW's "measure"): times, on scratch device buffers of the
  * plan's size allocated and freed inside the call, `reps` launches of every compiled
  * kernel that can run each pass of this plan (single pass: every rows kernel for its n
- * and layout, with each landing-buffer and refill variant, elements per thread and tile
- * height; four-step: every column kernel for pass 1, with and without the L2 prefetch,
- * and every transposed-row kernel for pass 2, for the plan's split n = M*K), and keeps
- * the fastest. Choices are cached per (n, batch, layout, direction) for the process, so a
- * second plan of the same shape is tuned without timing. Synchronises the device; do not
- * call it while the plan executes. Mixed-radix, multidimensional, uneven and tensor-core
- * plans are returned unchanged. reps in [1, 1000].
+ * and layout, with each landing-buffer and refill variant, elements per thread (the radix
+ * of the stages) and tile height; four-step: every split n = M*K with compiled kernels for
+ * both factors, and for each split every column kernel for pass 1, with and without the
+ * L2 prefetch, and every transposed-row kernel for pass 2), and keeps the fastest
+ * (fftc_plan_split and fftc_plan_info then report the chosen split and radices).
+ * Two-pass mixed-radix plans: the divisor splits n = M*K closest to sqrt(n) (six at most)
+ * are built and timed whole, and the plan is rebuilt with the fastest. Multidimensional
+ * plans: the last axis' 1D plan is tuned as above, and every strided power-of-two axis
+ * keeps the faster of its compiled column pass and the runtime-radix pass. Choices are
+ * cached per shape for the process, so a second plan of the same shape is tuned without
+ * timing. Synchronises the device; do not call it while the plan executes. Uneven and
+ * tensor-core plans are returned unchanged. reps in [1, 1000].
  */
 fftc_status fftc_plan_tune(fftc_plan plan, int reps);
 

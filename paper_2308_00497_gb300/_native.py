@@ -37,6 +37,7 @@ PROTOTYPES = {
     "fftc_plan_create_uneven": (_vp, [_c_i64, _vp, _vp, _vp, _c_int, _c_int]),
     "fftc_plan_create_nd": (_vp, [_c_int, _vp, _c_i64, _c_int, _c_int, _c_int]),
     "fftc_plan_tune": (_c_int, [_vp, _c_int]),
+    "fftc_plan_split": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "fftc_plan_check": (_c_int, [_vp, _vp]),
     "fftc_execute_pointwise": (_c_int, [_vp, _vp, _vp, _vp, ctypes.c_float, _vp]),
     "fftc_plan_timing": (_c_int, [_vp, _c_int]),

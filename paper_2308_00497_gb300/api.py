@@ -50,6 +50,12 @@ class Plan:
         nat.check(nat.load().fftc_plan_info(self._h, ctypes.byref(p), r, ctypes.byref(c)), "fftc_plan_info")
         return p.value, [r[i] for i in range(min(c.value, 16))]
 
+    def split(self):
+        """(M, K), M * K = n: the lengths of the pass-1 and pass-2 transforms (n, 1 for one pass)."""
+        m, k = ctypes.c_int64(0), ctypes.c_int64(0)
+        nat.check(nat.load().fftc_plan_split(self._h, ctypes.byref(m), ctypes.byref(k)), "fftc_plan_split")
+        return m.value, k.value
+
     def _shape(self):
         fp64 = self.precision == "fp64"
         if self.layout == "interleaved":
@@ -97,8 +103,10 @@ class Plan:
         return host_out
 
     def tune(self, reps: int = 5):
-        """Time every compiled kernel that can run this plan's passes; keep the fastest
-        (fftc_plan_tune, cached per shape for the process)."""
+        """Measure-mode planning (fftc_plan_tune): time the candidate decompositions (the
+        split n = M K, each pass's kernels and radix schedules; for multidimensional plans
+        the last axis and the strided axes' kernels) and keep the fastest, cached per shape
+        for the process."""
         with torch.cuda.device(self.device):
             nat.check(nat.load().fftc_plan_tune(self._h, int(reps)), "fftc_plan_tune")
         return self

@@ -21,14 +21,14 @@ namespace fftc {
 // ---------------------------------------------------------------------------
 // schedule mirror and registry
 // ---------------------------------------------------------------------------
-HostSched host_sched(int logl, int loge, bool rem_first) {
+HostSched host_sched(int logl, int loge) {
     HostSched h{};
     if (loge > logl) loge = logl;
     h.S = (logl + loge - 1) / loge;
     const int rem = logl % loge;
     int acc = 0;
     for (int s = 0; s < h.S; ++s) {
-        h.lr[s] = (rem && (rem_first ? s == 0 : s == h.S - 1)) ? rem : loge;
+        h.lr[s] = (rem && s == h.S - 1) ? rem : loge;
         h.lns[s] = acc;
         acc += h.lr[s];
     }
@@ -52,7 +52,7 @@ const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin,
 const KernelEntry *find_pipe_rows(int logl, int lay) {
     for (int i = 0; i < kernel_count(); ++i) {
         const KernelEntry *e = kernel_at(i);
-        if (e->pipe > 0 && e->kind == KIND_ROWS && e->logl == logl && e->lin == lay) return e;
+        if (e->pipe > 0 && e->prec == 0 && e->kind == KIND_ROWS && e->logl == logl && e->lin == lay) return e;
     }
     return nullptr;
 }
@@ -99,8 +99,8 @@ static float2 omega_f32(int64_t e, int64_t L) {
     return make_float2((float)c, (float)-s);
 }
 
-void stage_twiddles(int logl, int loge, std::vector<float2> &out, bool rem_first) {
-    HostSched h = host_sched(logl, loge, rem_first);
+void stage_twiddles(int logl, int loge, std::vector<float2> &out) {
+    HostSched h = host_sched(logl, loge);
     out.assign(h.tw_total > 0 ? h.tw_total : 1, make_float2(1.f, 0.f));
     int off = 0;
     for (int s = 1; s < h.S; ++s) {
@@ -166,6 +166,15 @@ cudaError_t plan_alloc(fftc_plan_s *p, size_t bytes, void **out) {
     cudaError_t e = cudaMalloc(out, bytes);
     if (e == cudaSuccess) p->dev_allocs.push_back(*out);
     return e;
+}
+
+void plan_release(fftc_plan_s *p, void *ptr) {
+    for (size_t i = 0; i < p->dev_allocs.size(); ++i)
+        if (p->dev_allocs[i] == ptr) {
+            cudaFree(ptr);
+            p->dev_allocs.erase(p->dev_allocs.begin() + (long)i);
+            return;
+        }
 }
 
 cudaError_t plan_upload(fftc_plan_s *p, const void *host, size_t bytes, void **out) {
@@ -259,12 +268,28 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
     const int nsched = plan->fs ? 2 : plan->npasses;
     for (int i = 0; i < nsched && !plan->uneven && !plan->mixed && !plan->nd; ++i) {
         const PassPlan &pp = plan->pass[i];
-        HostSched h = host_sched(pp.logl, pp.loge, plan->precision != FFTC_FP32);
+        HostSched h = host_sched(pp.logl, pp.loge);
         for (int s = 0; s < h.S && cnt < 32; ++s) tmp[cnt++] = 1 << h.lr[s];
     }
     if (radices)
         for (int i = 0; i < cnt && i < 16; ++i) radices[i] = tmp[i];
     if (n_radices) *n_radices = cnt;
+    return FFTC_OK;
+}
+
+fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k) {
+    if (!is_live(plan)) return FFTC_ERR_INVALID_PLAN;
+    if (plan->uneven || plan->nd) return FFTC_ERR_INVALID_VALUE;
+    int64_t mm = plan->n, kk = 1;
+    if (plan->mixed) {
+        mm = mixed_plan_split(plan);
+        kk = plan->n / mm;
+    } else if (plan->npasses == 2 || plan->fs) {
+        mm = int64_t(1) << plan->pass[0].logl;
+        kk = plan->n / mm;
+    }
+    if (m) *m = mm;
+    if (k) *k = kk;
     return FFTC_OK;
 }
 

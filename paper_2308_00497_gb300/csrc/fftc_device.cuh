@@ -110,14 +110,13 @@ __host__ __device__ __forceinline__ void dft(float2 *a) {
 
 // ---------------------------------------------------------------------------
 // Radix schedule of one line of length L = 2^LOGL with E = 2^LOGE elements per
-// thread: S stages of radix E, except that when LOGE does not divide LOGL one stage
-// takes the remainder radix 2^(LOGL mod LOGE): the last stage (REM_FIRST = false,
-// the CUDA-core kernels) or the first (REM_FIRST = true, the tensor-core kernels).
+// thread: S stages of radix E, except that when LOGE does not divide LOGL the last
+// stage takes the remainder radix 2^(LOGL mod LOGE).
 // Stage s has sub-transform length Ns = product of the earlier radices (the
 // Stockham "Ns"). Per-stage twiddle tables (stage s >= 1) hold w_{Ns R}^{t k} at
 // [(t-1) Ns + k], t = 1..R-1, k < Ns, concatenated in stage order.
 // ---------------------------------------------------------------------------
-template <int LOGL, int LOGE, bool REM_FIRST = false>
+template <int LOGL, int LOGE>
 struct Sched {
     static_assert(LOGE >= 1 && LOGE <= LOGL, "need 2 <= E <= L");
     static constexpr int L = 1 << LOGL;
@@ -126,7 +125,7 @@ struct Sched {
     static constexpr int S = (LOGL + LOGE - 1) / LOGE;
     static constexpr int REM = LOGL % LOGE;
     __host__ __device__ static constexpr int lr(int s) {
-        return (REM && (REM_FIRST ? s == 0 : s == S - 1)) ? REM : LOGE;
+        return (REM && s == S - 1) ? REM : LOGE;
     }
     __host__ __device__ static constexpr int lns(int s) {
         int acc = 0;

@@ -132,6 +132,8 @@ fftc_status fs_build(fftc_plan_s *p) {
     a.ctrl = s->ctrl;
     a.err = p->d_err;
     a.spin_limit = (long long)env_int_fs("FFTC_SPIN_LIMIT", 20000000);
+    // test hook: every wait is for a count nothing reaches, so each one runs out
+    a.wait_bias = env_int_fs("FFTC_TEST_UNREACHABLE_WAIT", 0) ? (1u << 30) : 0u;
     a.group_elems = gt * n;
     a.batch = B;
     a.gt = gt;

@@ -12,6 +12,7 @@ struct FsArgs {
     unsigned int *ctrl;     // [0] next item, [1 + g] pass-1 done of group g, [1 + G + g] pass-2 done
     int *err;
     long long spin_limit;
+    unsigned int wait_bias;  // added to every awaited count: 0, or (test hook) out of reach
     int64_t group_elems;    // GT * n complex elements per group
     int64_t batch, gt;      // transforms in the batch and per group
     int32_t groups, ring, tiles1, tiles2;
@@ -26,6 +27,7 @@ __device__ __forceinline__ unsigned int fs_ld_acquire(const unsigned int *p) {
 __device__ __forceinline__ void fs_wait(const FsArgs &a, const unsigned int *cnt, unsigned int target) {
     if (threadIdx.x == 0) {
         long long spins = 0;
+        target += a.wait_bias;
         while (fs_ld_acquire(cnt) < target) {
             if (++spins > a.spin_limit) {
                 atomicExch(a.err, 1);

@@ -52,6 +52,13 @@ struct PassParams {
     // the number of CTAs resident at once)
     int32_t pf_tiles;
     int *err;  // device error word of the plan (bounded waits that gave up)
+    // bounded waits of the pipelined kernels: poll limit (0 = the default), and a test
+    // hook that makes every wait run out (the kernels then issue no copy at all)
+    int64_t spin_limit;
+    int32_t test_no_copy;
+    // tensor-core passes: the fftc_precision of their radix-16 stages (FP16 or BF16, plain
+    // or hi + lo split); 0 for the CUDA-core passes
+    int32_t tc_mode;
 };
 
 typedef cudaError_t (*LaunchFn)(const PassParams &, cudaStream_t);
@@ -83,6 +90,6 @@ struct HostSched {
     int lns[32];
     int tw_total;
 };
-HostSched host_sched(int logl, int loge, bool rem_first = false);
+HostSched host_sched(int logl, int loge);
 
 }  // namespace fftc

@@ -8,6 +8,9 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "fftc_mixed.cuh"
@@ -34,6 +37,7 @@ static bool is_fp64(const fftc_plan_s *p) { return p->precision == FFTC_FP64; }
 
 struct MixedState {
     int npasses = 0;
+    int64_t m = 0;  // the split n = M K of a two-pass plan
     MixedPass pass[2];
 };
 
@@ -238,9 +242,12 @@ fftc_status mixed_build(fftc_plan_s *p) {
         return mixed_pass_setup(p, mp, n, C >= 4 ? C / 4 * 4 : C, KIND_ROWS, lay, lay, 1);
     }
     // n = M K with both factors at most one CTA's line, M as close to sqrt(n) as possible
-    const int64_t M = mixed_split(n, fp64);
+    // unless measure-mode planning chose another split
+    const bool forced = p->force_m > 1 && n % p->force_m == 0 && p->force_m <= single && n / p->force_m <= single;
+    const int64_t M = forced ? p->force_m : mixed_split(n, fp64);
     if (M == 0) return FFTC_ERR_UNSUPPORTED_SIZE;
     const int64_t K = n / M;
+    ms->m = M;
     ms->npasses = p->npasses = 2;
     const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
     if (plan_alloc(p, (size_t)(n * B) * esz, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
@@ -425,7 +432,8 @@ fftc_status nd_build(fftc_plan_s *p, int rank, const int64_t *dims) {
                 }
                 if (k->prepare() != cudaSuccess) return FFTC_ERR_CUDA;
                 nd->fast[ax] = k;
-                continue;
+                // the runtime-radix pass of the axis is built too: measure-mode planning
+                // may prefer it
             }
         }
         MixedPass &mp = nd->axes[ax];
@@ -493,6 +501,176 @@ int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap) {
 void mixed_free(fftc_plan_s *p) {
     delete p->mixed;
     p->mixed = nullptr;
+}
+
+int64_t mixed_plan_split(const fftc_plan_s *p) {
+    return (p->mixed && p->mixed->npasses == 2) ? p->mixed->m : p->n;
+}
+
+// ---------------------------------------------------------------------------
+// measure-mode planning (the runtime decomposition search of Section 6)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneBufs {
+    void *in = nullptr, *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~TuneBufs() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (st) cudaStreamDestroy(st);
+        if (in) cudaFree(in);
+        if (out) cudaFree(out);
+    }
+    bool init(size_t bytes) {
+        return cudaMalloc(&in, bytes) == cudaSuccess && cudaMalloc(&out, bytes) == cudaSuccess &&
+               cudaMemset(in, 0, bytes) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    }
+    // mean milliseconds of `reps` runs of fn(stream) after one untimed run; < 0 on failure
+    template <class F>
+    float time(F fn, int reps) {
+        if (!fn(st) || cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        cudaEventRecord(a, st);
+        for (int i = 0; i < reps; ++i) fn(st);
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) return -1.f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms / reps;
+    }
+};
+
+std::mutex g_mixed_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int, int, int>, int64_t> g_mixed_tune_cache;
+
+// a plan of p's shape built with the split n = m (n / m); nullptr on failure
+fftc_plan_s *mixed_candidate(const fftc_plan_s *p, int64_t m) {
+    fftc_plan_s *q = new (std::nothrow) fftc_plan_s();
+    if (!q) return nullptr;
+    q->magic = p->magic;
+    q->device = p->device;
+    q->n = p->n;
+    q->logn = p->logn;
+    q->batch = p->batch;
+    q->layout = p->layout;
+    q->direction = p->direction;
+    q->precision = p->precision;
+    q->force_m = m;
+    if (plan_build(q) != FFTC_OK) {
+        plan_destroy_extra(q);
+        plan_free_device(q);
+        delete q;
+        return nullptr;
+    }
+    return q;
+}
+
+void drop_candidate(fftc_plan_s *q) {
+    plan_destroy_extra(q);
+    plan_free_device(q);
+    delete q;
+}
+
+}  // namespace
+
+fftc_status mixed_tune(fftc_plan_s *p, int reps) {
+    if (!p->mixed || p->mixed->npasses != 2) return FFTC_OK;  // one pass: nothing to choose
+    const bool fp64 = is_fp64(p);
+    const int64_t n = p->n, single = fp64 ? kMixedSinglePass64 : kMixedSinglePass;
+    const auto key = std::make_tuple(n, p->batch, (int)p->layout, (int)p->direction, (int)p->precision);
+    int64_t best = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mixed_tune_mu);
+        auto it = g_mixed_tune_cache.find(key);
+        if (it != g_mixed_tune_cache.end()) best = it->second;
+    }
+    if (!best) {
+        // candidate splits: divisors with both factors within one CTA's line, the six closest
+        // to sqrt(n) (on a log scale)
+        std::vector<int64_t> cand;
+        for (int64_t m = 2; m <= single; ++m)
+            if (n % m == 0 && n / m <= single) cand.push_back(m);
+        const double c = 0.5 * std::log((double)n);
+        std::sort(cand.begin(), cand.end(), [&](int64_t x, int64_t y) {
+            return std::fabs(std::log((double)x) - c) < std::fabs(std::log((double)y) - c);
+        });
+        if (cand.size() > 6) cand.resize(6);
+        TuneBufs tb;
+        if (!tb.init((size_t)p->total_elems * (fp64 ? 16 : 8))) return FFTC_ERR_ALLOC;
+        float tbest = 1e30f;
+        for (int64_t m : cand) {
+            fftc_plan_s *q = mixed_candidate(p, m);
+            if (!q) continue;
+            const float t = tb.time([&](cudaStream_t st) { return mixed_run(q, tb.in, tb.out, nullptr, 0.f, st) == FFTC_OK; },
+                                    reps);
+            drop_candidate(q);
+            if (t > 0.f && t < tbest) {
+                tbest = t;
+                best = m;
+            }
+        }
+        if (!best) return FFTC_OK;
+        std::lock_guard<std::mutex> lk(g_mixed_tune_mu);
+        g_mixed_tune_cache[key] = best;
+    }
+    if (best == p->mixed->m) return FFTC_OK;
+    // rebuild the plan's device state with the chosen split (the handle and its timing
+    // probe stay the same)
+    fftc_plan_s *q = mixed_candidate(p, best);
+    if (!q) return FFTC_ERR_ALLOC;
+    mixed_free(p);
+    plan_free_device(p);
+    p->force_m = best;
+    p->npasses = q->npasses;
+    p->workspace = q->workspace;
+    p->tw2_full = q->tw2_full;
+    p->d_err = q->d_err;
+    p->mixed = q->mixed;
+    p->dev_allocs.swap(q->dev_allocs);
+    q->mixed = nullptr;
+    q->dev_allocs.clear();
+    delete q;
+    return FFTC_OK;
+}
+
+fftc_status nd_tune(fftc_plan_s *p, int reps) {
+    NdState *nd = p->nd;
+    if (!nd) return FFTC_OK;
+    fftc_status s = plan_tune(nd->rows, reps);  // the last axis: a 1D plan
+    if (s != FFTC_OK) return s;
+    TuneBufs tb;
+    bool ready = false;
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    for (int i = 0; i < nd->naxes; ++i) {
+        if (!nd->fast[i]) continue;  // only the runtime-radix pass exists for this axis
+        if (!ready) {
+            if (!tb.init((size_t)p->total_elems * (is_fp64(p) ? 16 : 8))) return FFTC_ERR_ALLOC;
+            ready = true;
+        }
+        const KernelEntry *k = nd->fast[i];
+        const float tf = tb.time([&](cudaStream_t st) {
+            PassParams q = nd->fastp[i];
+            q.in = (const float *)tb.out;
+            q.out = (float *)tb.out;
+            q.conj_in = q.conj_out = inv;
+            return k->launch(q, st) == cudaSuccess;
+        }, reps);
+        const float tm = tb.time([&](cudaStream_t st) {
+            MixedArgs a = nd->axes[i].args;
+            a.p.in = (const float *)tb.out;
+            a.p.out = (float *)tb.out;
+            a.p.conj_in = a.p.conj_out = inv;
+            return mixed_launch(nd->axes[i], a, st) == cudaSuccess;
+        }, reps);
+        if (tm > 0.f && (tf <= 0.f || tm < tf)) nd->fast[i] = nullptr;
+    }
+    return FFTC_OK;
 }
 
 }  // namespace fftc

@@ -28,8 +28,11 @@
 // the other factor 2^LOGX of n = M K, a compile-time constant when LOGX > 0.
 #pragma once
 
+#include <algorithm>
+
 #include "fftc_device.cuh"
 #include "fftc_internal.h"
+#include "fftc_tc.cuh"
 
 namespace fftc {
 
@@ -46,7 +49,13 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0>
+// 128-byte aligned start of dynamic shared memory (the tensor-core area when TC is set)
+__device__ __forceinline__ unsigned char *dyn_smem_base128() {
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    return dyn_raw + ((128 - (smem_u32(dyn_raw) & 127)) & 127);
+}
+
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0, bool TC = false>
 struct Pass {
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
@@ -54,7 +63,24 @@ struct Pass {
     static constexpr int C_LINES = C, LIN_LAYOUT = LIN, KIND_ID = KIND;
     static constexpr int LINE_WORDS = L + (L >> LOGE);
     static constexpr int PITCH = pass_pitch(LINE_WORDS, C);
-    static constexpr int SMEM = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
+    // TC: radix-16 stages on the tensor cores (fftc_tc.cuh); the tensor-core area sits in
+    // front of the data in dynamic shared memory, and a stage's A rows alias the tile buffer
+    static constexpr int TC_BYTES = TC ? kTcAreaBytes : 0;
+    static constexpr int DATA_BYTES = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
+    static constexpr int SMEM = TC ? TC_BYTES + DATA_BYTES + 128 : DATA_BYTES;
+    static_assert(!TC || (LOGE == 4 && NT % 128 == 0 && !IDX), "tensor-core passes: 16 elements per thread");
+    static_assert(!TC || DATA_BYTES >= NT * 128, "the A rows must fit in the tile buffer");
+    __host__ __device__ static constexpr int tc_count(int upto) {
+        int c = 0;
+        for (int i = 0; i < upto; ++i) c += (Sc::lr(i) == 4) ? 1 : 0;
+        return c;
+    }
+    static constexpr int NTC = TC ? tc_count(S) : 0;  // radix-16 stages per tile
+    __host__ __device__ static constexpr float tc_out_scale() {
+        float f = 1.f;
+        for (int i = 0; i < NTC; ++i) f *= 4.f;
+        return f;
+    }
     static constexpr bool IN_TAU = (KIND != KIND_COLS);
     static constexpr bool OUT_TAU = (KIND == KIND_ROWS);
     static constexpr bool MID_TAU = (C < 16);
@@ -158,6 +184,12 @@ struct Pass {
                                          __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
                     }
                 }
+                if constexpr (TC) {
+                    if (!tc_is_bf16(p.tc_mode)) {  // FP16 stages ran on data scaled by 1/4 each
+                        x.x *= tc_out_scale();
+                        x.y *= tc_out_scale();
+                    }
+                }
                 if (p.post_h) {
                     const int a = a0 + t * (L / R);
                     const float h = __ldg(p.post_h + l * (int)p.post_line_mul + a * (int)p.post_elem_mul) * p.post_scale;
@@ -213,11 +245,13 @@ struct Pass {
         }
     }
 
+    // `tk`: how many tiles this CTA transformed before this one (tensor-core mbarrier phases)
     template <int s, bool LANDED = false, class H = NoHook>
     __device__ __forceinline__ static void stage(const PassParams &p, float2 *sm, float2 (&v)[E], int tid, int64_t g0,
-                                                 const H &hook = H()) {
+                                                 const H &hook = H(), uint32_t tk = 0) {
         constexpr int LR = Sc::lr(s), R = 1 << LR, LNS = Sc::lns(s), NS = 1 << LNS;
         constexpr bool TF = tau_fast(s);
+        constexpr bool TCS = TC && LR == 4;  // this stage's butterfly runs on the tensor cores
         const int c = TF ? tid / TPL : tid % C;
         const int tau = TF ? tid % TPL : tid / C;
         const int64_t g = g0 + c;
@@ -241,7 +275,7 @@ struct Pass {
                     for (int t = 0; t < R; ++t) v[q * R + t] = src[t * (L / R)];
                 }
             }
-            if constexpr (H::active && s == S - 1) {
+            if constexpr (H::active && s == S - 1 && !TCS) {
                 __syncthreads();  // the last shared read of the tile is done: the buffer is free
                 hook();
             }
@@ -253,11 +287,20 @@ struct Pass {
                 for (int t = 1; t < R; ++t) v[q * R + t] = cmul(v[q * R + t], __ldg(twk + (t - 1) * NS));
             }
         }
+        if constexpr (TCS) {
+            if constexpr (s > 0 || LANDED) __syncthreads();  // every read of the buffer the A rows alias is done
+            // the i-th tensor-core stage of this CTA's k-th tile uses mbarrier phase (k NTC + i) mod 2
+            const uint32_t phase = (tk * NTC + tc_count(s)) & 1u;
+            TcUnit<NT>::dft16(p, v, dyn_smem_base128(), smem_u32(sm), phase);
+            __syncthreads();  // every group's MMA has read its A rows
+            if constexpr (H::active && s == S - 1) hook();  // the tile buffer is free
+        } else {
 #pragma unroll
-        for (int q = 0; q < E / R; ++q) dft<R>(v + q * R);
+            for (int q = 0; q < E / R; ++q) dft<R>(v + q * R);
+        }
 
         if constexpr (s < S - 1) {
-            if constexpr (s > 0 || LANDED) sync();  // every read of this stage precedes any overwrite
+            if constexpr ((s > 0 || LANDED) && !TCS) sync();  // every read of this stage precedes any overwrite
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
                 const int j = tau + q * TPL;
@@ -272,7 +315,7 @@ struct Pass {
                 }
             }
             sync();
-            stage<s + 1, LANDED>(p, sm, v, tid, g0, hook);
+            stage<s + 1, LANDED>(p, sm, v, tid, g0, hook, tk);
         } else {
             store_global<R>(p, v, tau, g, live);
         }
@@ -302,10 +345,26 @@ struct Pass {
 
     __device__ __forceinline__ static void run(const PassParams &p) {
         extern __shared__ float2 sm_dyn[];
-        if constexpr (KIND == KIND_COLS && !IDX)
+        if constexpr (KIND == KIND_COLS && !IDX && !TC)
             if (p.pf_tiles > 0) prefetch_tile(p, (int64_t)blockIdx.x + p.pf_tiles);
         float2 v[E];
-        stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
+        if constexpr (TC) {
+            // persistent: the set-up (DFT matrices, mbarriers, TMEM columns) is paid once per CTA
+            unsigned char *area = dyn_smem_base128();
+            float2 *sm = reinterpret_cast<float2 *>(area + TC_BYTES);
+            TcUnit<NT>::setup(p, area);
+            const int64_t ntiles = (p.total_lines + C - 1) / C;
+            uint32_t tk = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tk) {
+                if constexpr (KIND == KIND_COLS)
+                    if (p.pf_tiles > 0) prefetch_tile(p, tile + gridDim.x);  // this CTA's next tile
+                stage<0>(p, sm, v, threadIdx.x, tile * C, NoHook(), tk);
+                __syncthreads();  // the tile's last shared reads precede the next tile's A rows
+            }
+            TcUnit<NT>::teardown(area);
+        } else {
+            stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
+        }
     }
 
     // one tile (C lines starting at line tile * C) with the caller's shared memory
@@ -318,65 +377,101 @@ struct Pass {
     // by every thread, as soon as the tile's last shared-memory read is done
     template <class H = NoHook>
     __device__ __forceinline__ static void run_tile_landed(const PassParams &p, int64_t tile, float2 *sm,
-                                                           const H &hook = H()) {
+                                                           const H &hook = H(), uint32_t tk = 0) {
         float2 v[E];
-        stage<0, true>(p, sm, v, threadIdx.x, tile * C, hook);
+        stage<0, true>(p, sm, v, threadIdx.x, tile * C, hook, tk);
     }
 };
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
-__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::NT,
-                                  Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::MINB)
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
+__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>::NT,
+                                  Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>::MINB)
     k_pass(const __grid_constant__ PassParams p) {
-    Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>::run(p);
+    Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>::run(p);
+}
+
+// CTAs of a kernel that fit on one SM at once. For kernels that allocate tensor memory
+// (tmem_cols > 0) the runtime's occupancy query answers one CTA per SM, while the SM holds
+// as many as its registers, shared memory, threads and 512 TMEM columns allow; those
+// limits are counted here instead.
+inline int resident_per_sm(const void *func, int threads, int dyn_smem, int tmem_cols) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, dyn_smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    if (tmem_cols <= 0) return per_sm;
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, resv = 0;
+    if (cudaFuncGetAttributes(&fa, func) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return per_sm > 0 ? per_sm : 1;
+    }
+    const int regs = (fa.numRegs + 7) / 8 * 8;  // registers are allocated 256 per warp
+    int n = thr_sm / threads;
+    if (regs > 0) n = std::min(n, regs_sm / (regs * threads));
+    n = std::min(n, smem_sm / (dyn_smem + (int)fa.sharedSizeBytes + resv));
+    n = std::min(n, 512 / tmem_cols);
+    return std::max(n, std::max(per_sm, 1));
 }
 
 // CTAs of a k_pass instance resident on the current device at once (0 if unknown)
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
 int resident_ctas() {
     static int r = -1;
     if (r < 0) {
-        using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
-        int per_sm = 0, sms = 0, dev = 0;
+        using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
+        int sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>, P::NT,
-                                                          P::SMEM) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;
+        const int per_sm = resident_per_sm((const void *)k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>, P::NT,
+                                           P::SMEM, TC ? (int)tc_tmem_cols(P::NT) : 0);
         r = per_sm * sms;
     }
     return r;
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
 cudaError_t launch_pass(const PassParams &p, cudaStream_t st) {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
     const int64_t blocks = (p.total_lines + C - 1) / C;
     if (blocks <= 0) return cudaSuccess;
+    if constexpr (TC) {  // persistent: one wave of CTAs walks the tiles
+        const int res = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>();
+        if (res <= 0) return cudaErrorInvalidConfiguration;
+        const unsigned grid = (unsigned)(blocks < res ? blocks : res);
+        k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC><<<grid, P::NT, P::SMEM, st>>>(p);
+        return cudaGetLastError();
+    }
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     if constexpr (KIND == KIND_COLS) {
         if (p.pf_tiles < 0) {
             PassParams q = p;
-            q.pf_tiles = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>();
-            k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(q);
+            q.pf_tiles = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>();
+            k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(q);
             return cudaGetLastError();
         }
     }
-    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
+    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
 cudaError_t prepare_pass() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
     if (P::SMEM <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
+    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX = 0>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX = 0, bool TC = false>
 constexpr KernelEntry entry() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
     return KernelEntry{KIND,
                        LOGL,
                        LOGE,
@@ -385,9 +480,9 @@ constexpr KernelEntry entry() {
                        LOUT,
                        P::NT,
                        P::SMEM,
-                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
-                       &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX>,
-                       0,
+                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>,
+                       &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>,
+                       TC ? 1 : 0,
                        LOGX,
                        0};
 }

@@ -25,70 +25,9 @@
 #include <cuda.h>
 
 #include "fftc_pass.cuh"
+#include "fftc_ptx.cuh"
 
 namespace fftc {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// order this thread's earlier generic-proxy shared accesses before later async-proxy writes
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 2D tensor box -> shared (128-byte aligned destination; x * element size a multiple of 16)
-__device__ __forceinline__ void tensor2d_g2s(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// bounded wait for the phase with the given parity: gives up after `limit` polls or
-// kMbarWaitNs nanoseconds, whichever comes first
-constexpr uint64_t kMbarWaitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
-    const uint64_t t0 = global_ns();
-    for (long long i = 0; i < limit; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 63 && global_ns() - t0 > kMbarWaitNs) return false;
-    }
-    return false;
-}
-
-constexpr long long kMbarSpinLimit = 1ll << 24;
 
 struct PipeArgs {
     PassParams p;
@@ -102,13 +41,15 @@ struct PipeTile {
     static constexpr int C = P::C_LINES, L = P::L;
     static constexpr int RAW_WORDS = C * P::PITCH > C * L ? C * P::PITCH : C * L;
     static constexpr int BUF_WORDS = (RAW_WORDS + 15) / 16 * 16;  // 128-byte multiple
-    static constexpr int SMEM = NBUF * BUF_WORDS * (int)sizeof(float2) + 128;  // + room to align the base
+    // + room to align the base, + the tensor-core area in front of the buffers (TC passes)
+    static constexpr int SMEM = NBUF * BUF_WORDS * (int)sizeof(float2) + 128 + P::TC_BYTES;
     static constexpr int NT = P::NT;
     static constexpr int BOXR = L < 256 ? L : 256;  // rows per tensor box (box dims <= 256)
 
     // thread 0: arm `bar` and start the copies of `tile` into `buf`
     __device__ __forceinline__ static void issue(const PipeArgs &a, int64_t tile, float2 *buf, uint64_t *bar) {
         const PassParams &p = a.p;
+        if (p.test_no_copy) return;  // test hook: the barrier is never armed, its wait runs out
         const int64_t g0 = tile * C;
         if constexpr (KIND == KIND_COLS) {
             const int tr = (int)(g0 >> p.log_lpt), b0 = (int)(g0 & ((int64_t(1) << p.log_lpt) - 1));
@@ -171,46 +112,49 @@ struct PipeTile {
 
     __device__ static void run(const PipeArgs &a) {
         const PassParams &p = a.p;
-        extern __shared__ __align__(128) unsigned char pipe_raw[];
         // tensor-copy destinations must be 128-byte aligned
-        float2 *bufs = reinterpret_cast<float2 *>(pipe_raw + ((128 - (smem_u32(pipe_raw) & 127)) & 127));
+        unsigned char *area = dyn_smem_base128();
+        float2 *bufs = reinterpret_cast<float2 *>(area + P::TC_BYTES);
         __shared__ __align__(8) uint64_t bars[NBUF];
         const int64_t ntiles = (p.total_lines + C - 1) / C;
         if (threadIdx.x == 0) {
             for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
             fence_mbar_init();
         }
+        if constexpr (P::NTC > 0) TcUnit<NT>::setup(p, area);  // ends with a CTA barrier
         __syncthreads();
         if (threadIdx.x == 0)
             for (int b = 0; b < NBUF; ++b) {
                 const int64_t t = blockIdx.x + (int64_t)b * gridDim.x;
                 if (t < ntiles) issue(a, t, bufs + b * BUF_WORDS, &bars[b]);
             }
+        const long long limit = p.spin_limit > 0 ? (long long)p.spin_limit : kMbarSpinLimit;
         for (int64_t k = 0;; ++k) {
             const int64_t tile = blockIdx.x + k * gridDim.x;
             if (tile >= ntiles) break;
             const int b = (int)(k % NBUF);
             const uint32_t parity = (uint32_t)((k / NBUF) & 1);
-            if (!mbar_wait_bounded(&bars[b], parity, kMbarSpinLimit)) {
+            if (!mbar_wait_bounded(&bars[b], parity, limit)) {
                 if (threadIdx.x == 0 && p.err) atomicExch(p.err, 2);
                 // let this CTA's other copies land before the shared memory goes away
                 for (int d = 1; d < NBUF; ++d) {
                     const int64_t kk = k + d;
                     if (blockIdx.x + kk * gridDim.x < ntiles)
-                        mbar_wait_bounded(&bars[kk % NBUF], (uint32_t)((kk / NBUF) & 1), kMbarSpinLimit);
+                        mbar_wait_bounded(&bars[kk % NBUF], (uint32_t)((kk / NBUF) & 1), limit);
                 }
-                return;
+                break;
             }
             const int64_t next = tile + (int64_t)NBUF * gridDim.x;
             float2 *buf = bufs + b * BUF_WORDS;
             if constexpr (EARLY) {
-                P::run_tile_landed(p, tile, buf, Refill{&a, next < ntiles ? next : -1, buf, &bars[b]});
+                P::run_tile_landed(p, tile, buf, Refill{&a, next < ntiles ? next : -1, buf, &bars[b]}, (uint32_t)k);
             } else {
-                P::run_tile_landed(p, tile, buf);
+                P::run_tile_landed(p, tile, buf, NoHook(), (uint32_t)k);
                 __syncthreads();  // every shared read of buffer b is done
                 if (next < ntiles) refill(a, next, buf, &bars[b]);
             }
         }
+        if constexpr (P::NTC > 0) TcUnit<NT>::teardown(area);
     }
 };
 
@@ -233,11 +177,10 @@ struct PipeLauncher {
         cudaError_t e =
             cudaFuncSetAttribute(k_pipe<P, NBUF, EARLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM);
         if (e != cudaSuccess) return e;
-        int per_sm = 0, sms = 0, dev = 0;
+        int sms = 0, dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipe<P, NBUF, EARLY>, PT::NT,
-                                                               PT::SMEM)) != cudaSuccess)
-            return e;
+        const int per_sm = resident_per_sm((const void *)k_pipe<P, NBUF, EARLY>, PT::NT, PT::SMEM,
+                                           P::NTC > 0 ? (int)tc_tmem_cols(PT::NT) : 0);
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid_cache() = (per_sm > 0 ? per_sm : 1) * sms;
         return cudaSuccess;
@@ -265,12 +208,13 @@ struct PipeLauncher {
 constexpr int pipe_code(int nbuf, bool early) { return nbuf | (early ? 4 : 0); }
 
 // registry entry of a pipelined pass kernel
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int NBUF, bool EARLY = false>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int NBUF, bool EARLY = false,
+          bool TC = false>
 constexpr KernelEntry pipe_entry() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
     using L = PipeLauncher<P, NBUF, EARLY>;
     return KernelEntry{KIND,          LOGL, LOGE, C, LIN, LOUT, P::NT, PipeTile<P, NBUF, EARLY>::SMEM,
-                       &L::launch,    &L::prepare, 0, LOGX, pipe_code(NBUF, EARLY)};
+                       &L::launch,    &L::prepare, TC ? 1 : 0, LOGX, pipe_code(NBUF, EARLY)};
 }
 
 }  // namespace fftc

@@ -112,9 +112,16 @@ static const PipeRowsDefault *pipe_rows_default(int logn) {
     return nullptr;
 }
 
+// bounded waits: FFTC_SPIN_LIMIT sets the poll limit of the pipelined kernels, and
+// FFTC_TEST_UNREACHABLE_WAIT (a test hook) makes them issue no copy so every wait runs out
+static void set_wait_hooks(PassParams &b) {
+    b.spin_limit = env_int("FFTC_SPIN_LIMIT", 0);
+    b.test_no_copy = env_int("FFTC_TEST_UNREACHABLE_WAIT", 0) ? 1 : 0;
+}
+
 static fftc_status upload_stage_tables(fftc_plan_s *p, PassPlan &pp) {
     std::vector<float2> tw;
-    stage_twiddles(pp.logl, pp.loge, tw, p->precision != FFTC_FP32);  // tensor-core kernels: remainder first
+    stage_twiddles(pp.logl, pp.loge, tw);
     void *d = nullptr;
     if (plan_upload(p, tw.data(), tw.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     pp.tw = (float2 *)d;
@@ -128,9 +135,66 @@ static fftc_status prepare(PassPlan &pp) {
     return FFTC_OK;
 }
 
+fftc_status upload_full_diagonal(fftc_plan_s *p, int logm, float2 **out) {
+    const int64_t n = p->n, M = int64_t(1) << logm, K = n >> logm;
+    std::vector<float2> full((size_t)n);
+    for (int64_t tp = 0; tp < M; ++tp)
+        for (int64_t b = 0; b < K; ++b) {
+            double c, s;
+            unit_root(tp * b, n, &c, &s);
+            full[(size_t)(tp * K + b)] = make_float2((float)c, (float)-s);
+        }
+    void *d = nullptr;
+    if (plan_upload(p, full.data(), full.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    *out = (float2 *)d;
+    return FFTC_OK;
+}
+
+void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams &b) {
+    const int64_t n = p->n, B = p->batch, M = int64_t(1) << logm, K = n >> logm;
+    const int logk = p->logn - logm;
+    const int64_t plane = p->layout == FFTC_LAYOUT_SPLIT ? n * B : 0;
+    const int tcm = p->precision != FFTC_FP32 ? (int)p->precision : 0;
+    memset(&a, 0, sizeof(a));
+    a.err = p->d_err;
+    set_wait_hooks(a);
+    a.in_plane = plane;
+    a.out_plane = 0;
+    a.total_lines = B * K;
+    a.log_lpt = logk;
+    a.in_tr = n;
+    a.in_line = 1;
+    a.in_elem = K;
+    a.out_tr = n;
+    a.out_line = 1;
+    a.out_elem = K;
+    a.tw2_lo = p->tw2_lo;
+    a.tw2_hi = p->tw2_hi;
+    a.tw2_full = p->tw2_full;
+    a.log_n2 = p->logn;
+    a.tw2_lo_bits = p->tw2_lo_bits;
+    a.tc_mode = tcm;
+    memset(&b, 0, sizeof(b));
+    b.err = p->d_err;
+    set_wait_hooks(b);
+    b.in_plane = 0;
+    b.out_plane = plane;
+    b.total_lines = B * M;
+    b.log_lpt = logm;
+    b.in_tr = n;
+    b.in_line = K;
+    b.in_elem = 1;
+    b.out_tr = n;
+    b.out_line = 1;
+    b.out_elem = M;
+    b.post_line_mul = 1;
+    b.post_elem_mul = M;
+    b.tc_mode = tcm;
+}
+
 fftc_status plan_build_passes(fftc_plan_s *p) {
-    const int prec = (int)p->precision;
-    const bool tc = prec != FFTC_FP32;
+    const bool tc = p->precision != FFTC_FP32;
+    const int prec = tc ? 1 : 0;  // registry tag of the tensor-core kernels (the mode is a run-time argument)
     if (tc && (p->logn < 7 || p->logn > 16)) return FFTC_ERR_UNSUPPORTED_SIZE;
     const int64_t n = p->n, B = p->batch;
     const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
@@ -141,12 +205,12 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     p->d_err = (int *)d;
     if (cudaMemset(p->d_err, 0, 16) != cudaSuccess) return FFTC_ERR_CUDA;
 
-    if (p->logn <= (tc ? 13 : env_int("FFTC_TUNE_MAX_SINGLE_LOG", kMaxSinglePassLog))) {
+    if (p->logn <= (tc ? kMaxSinglePassLog : env_int("FFTC_TUNE_MAX_SINGLE_LOG", kMaxSinglePassLog))) {
         PassPlan &pp = p->pass[0];
         p->npasses = 1;
         pp.kind = KIND_ROWS;
         pp.logl = p->logn;
-        if (tc) {
+        if (tc) {  // 16 elements per thread; 256-thread tiles up to 2^12, one line per tile above
             pp.loge = 4;
             pp.lines = p->logn >= 12 ? 1 : (4096 >> p->logn);
         } else if (!choose_rows(p->logn, lay, &pp.loge, &pp.lines)) {
@@ -154,6 +218,8 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         }
         pp.lin = pp.lout = lay;
         pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay, prec);
+        if (tc && !pp.k)  // n >= 2^9: bulk-copy fed (two landing buffers up to 2^12, one above)
+            pp.k = find_kernel(KIND_ROWS, pp.logl, 4, pp.lines, lay, lay, prec, 0, p->logn <= 12 ? 6 : 5);
         // pipelined persistent kernel where it measured faster (n = 2^9 .. 2^14)
         const PipeRowsDefault *pd = pipe_rows_default(p->logn);
         if (!tc && env_int("FFTC_PIPE", pd ? 1 : 0)) {
@@ -164,7 +230,8 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
             if (!k) k = find_pipe_rows(pp.logl, lay);
             for (int i = 0; (pe || pc || pk) && i < kernel_count(); ++i) {
                 const KernelEntry *e = kernel_at(i);
-                if (e->pipe && e->kind == KIND_ROWS && e->logl == pp.logl && e->lin == lay && (!pe || e->loge == pe) &&
+                if (e->pipe && e->prec == 0 && e->kind == KIND_ROWS && e->logl == pp.logl && e->lin == lay &&
+                    (!pe || e->loge == pe) &&
                     (!pc || e->lines == pc) && (!pk || e->pipe == pk))
                     k = e;
             }
@@ -177,6 +244,8 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.err = p->d_err;
+        set_wait_hooks(b);
+        b.tc_mode = tc ? (int)p->precision : 0;
         b.in_plane = b.out_plane = plane;
         b.total_lines = B;
         b.log_lpt = 0;
@@ -192,9 +261,12 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
 
     // four-step: n = M * K
     int logm, e1, e2, c1 = kPassLines, c2 = kPassLines, p1code = 0, p2code = 0, pf = 0;
-    if (tc) {
+    if (tc) {  // the FP32 shapes of 2^15 and 2^16 with 16 elements per thread, bulk-copy fed
         logm = p->logn / 2;
         e1 = e2 = 4;
+        p1code = env_int("FFTC_TUNE_TC_P1", 5);  // tensor-map boxes, one landing buffer (0: plain loads)
+        p2code = env_int("FFTC_TUNE_TC_P2", 6);  // one bulk copy per tile, two buffers (0: plain loads)
+        pf = p1code ? 0 : 1;
     } else {
         const FourStepChoice fc = choose_four_step(p->logn, lay);
         logm = fc.logm;
@@ -207,7 +279,6 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         pf = fc.pf;
     }
     const int logk = p->logn - logm;
-    const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
     p->npasses = 2;
     const bool l2res = !tc && fs_available(p->logn, lay);
     if (!l2res) {  // the L2-resident executor owns a small workspace ring instead
@@ -233,19 +304,9 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
     p->tw2_lo = (float2 *)d;
     if (plan_upload(p, hi.data(), hi.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     p->tw2_hi = (float2 *)d;
-    // the whole diagonal D^n_M of Eq. 1 in pass-1 layout: entry t' * K + b = w_n^(b t');
-    // above 2^20 points (8 MB) pass 1 takes the product of the two small tables instead,
-    // which stay in L1 and L2 where a table of n entries would not
     if (p->logn <= 20) {
-        std::vector<float2> full((size_t)n);
-        for (int64_t tp = 0; tp < M; ++tp)
-            for (int64_t b = 0; b < K; ++b) {
-                double c, s;
-                unit_root(tp * b, n, &c, &s);
-                full[(size_t)(tp * K + b)] = make_float2((float)c, (float)-s);
-            }
-        if (plan_upload(p, full.data(), full.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
-        p->tw2_full = (float2 *)d;
+        fftc_status s = upload_full_diagonal(p, logm, &p->tw2_full);
+        if (s != FFTC_OK) return s;
     }
 
     {   // pass 1: columns
@@ -263,25 +324,8 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         if (p1code && !pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0, p1code);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logk);
         if (!pp.k) pp.k = find_kernel(KIND_COLS, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
-        PassParams &b = pp.base;
-        memset(&b, 0, sizeof(b));
-        b.err = p->d_err;
-        b.in_plane = plane;
-        b.out_plane = 0;
-        b.total_lines = B * K;
-        b.log_lpt = logk;
-        b.in_tr = n;
-        b.in_line = 1;
-        b.in_elem = K;
-        b.out_tr = n;
-        b.out_line = 1;
-        b.out_elem = K;
-        b.tw2_lo = p->tw2_lo;
-        b.tw2_hi = p->tw2_hi;
-        b.tw2_full = p->tw2_full;
-        b.log_n2 = p->logn;
-        b.tw2_lo_bits = p->tw2_lo_bits;
-        b.pf_tiles = pf ? -1 : 0;
+        four_step_params(p, logm, pp.base, p->pass[1].base);
+        pp.base.pf_tiles = pf ? -1 : 0;
         fftc_status s = upload_stage_tables(p, pp);
         if (s != FFTC_OK) return s;
         if ((s = prepare(pp)) != FFTC_OK) return s;
@@ -299,21 +343,6 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         if (p2code && !pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0, p2code);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, logm);
         if (!pp.k) pp.k = find_kernel(KIND_ROWST, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, prec, 0);
-        PassParams &b = pp.base;
-        memset(&b, 0, sizeof(b));
-        b.err = p->d_err;
-        b.in_plane = 0;
-        b.out_plane = plane;
-        b.total_lines = B * M;
-        b.log_lpt = logm;
-        b.in_tr = n;
-        b.in_line = K;
-        b.in_elem = 1;
-        b.out_tr = n;
-        b.out_line = 1;
-        b.out_elem = M;
-        b.post_line_mul = 1;
-        b.post_elem_mul = M;
         fftc_status s = upload_stage_tables(p, pp);
         if (s != FFTC_OK) return s;
         if ((s = prepare(pp)) != FFTC_OK) return s;

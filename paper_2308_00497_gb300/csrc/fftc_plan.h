@@ -49,6 +49,7 @@ struct fftc_plan_s {
     fftc::FsState *fs = nullptr;
     fftc::MixedState *mixed = nullptr;  // n with factors 3, 5 or 7 (fftc_mixed.cu)
     fftc::NdState *nd = nullptr;        // rank 2 / 3 transforms (fftc_mixed.cu)
+    int64_t force_m = 0;  // mixed radix: the split n = M K chosen by measure-mode planning (0: default)
     std::vector<void *> dev_allocs;
     // timing probe: events[slot * 3 + i] before pass i (i < npasses) and after the last
     std::vector<cudaEvent_t> probe_events;
@@ -62,6 +63,13 @@ struct fftc_plan_s {
 namespace fftc {
 
 fftc_status plan_build(fftc_plan_s *p);
+// Four-step pieces for the split n = 2^logm * 2^(logn - logm) (Eq. 1 at the memory level):
+// the whole inter-pass diagonal in pass-1 layout (n entries, uploaded as a plan allocation),
+// and both passes' parameters from the plan's tables (kernels and stage tables aside)
+fftc_status upload_full_diagonal(fftc_plan_s *p, int logm, float2 **out);
+void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams &b);
+// release one device allocation made through plan_alloc / plan_upload
+void plan_release(fftc_plan_s *p, void *ptr);
 // Enqueue the plan on `st`. post_h (device, n floats, may be NULL) multiplies every
 // output frequency k by post_h[k] * post_scale.
 fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
@@ -80,7 +88,7 @@ cudaError_t plan_alloc(fftc_plan_s *p, size_t bytes, void **out);
 cudaError_t plan_upload(fftc_plan_s *p, const void *host, size_t bytes, void **out);
 
 void unit_root(int64_t m, int64_t L, double *cosv, double *sinv);
-void stage_twiddles(int logl, int loge, std::vector<float2> &out, bool rem_first = false);
+void stage_twiddles(int logl, int loge, std::vector<float2> &out);
 
 // uneven batches (fftc_uneven.cu)
 fftc_status uneven_build(fftc_plan_s *p, int64_t count, const int64_t *n, const int8_t *dir, const int64_t *off);
@@ -96,6 +104,11 @@ fftc_status mixed_run(fftc_plan_s *p, const void *in, void *out, const float *po
                       cudaStream_t st);
 int mixed_radix_list(const fftc_plan_s *p, int *radices, int cap);
 void mixed_free(fftc_plan_s *p);
+// measure-mode planning of mixed-radix plans (the split n = M K) and multidimensional plans
+// (the last axis' 1D plan, and compiled versus runtime-radix kernels of the strided axes)
+fftc_status mixed_tune(fftc_plan_s *p, int reps);
+int64_t mixed_plan_split(const fftc_plan_s *p);  // M of a two-pass mixed plan, n for one pass
+fftc_status nd_tune(fftc_plan_s *p, int reps);
 
 // time every compiled kernel that can run each pass of the plan and keep the fastest
 // (fftc_tune.cu)

@@ -3,10 +3,10 @@
 
 namespace fftc {
 
-extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcF16Table[],
-    kTcBf16Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[],
+extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcRowsTable[],
+    kTc4Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[],
     kColsSplitTable[], kLargeTable[], kPipeLargeTable[];
-extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcF16Count, kTcBf16Count,
+extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcRowsCount, kTc4Count,
     kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount, kColsSplitCount, kLargeCount, kPipeLargeCount;
 
 struct TableRef {
@@ -16,7 +16,7 @@ struct TableRef {
 static const TableRef kTables[] = {
     {kRowsIlTable, &kRowsIlCount}, {kRowsSplitTable, &kRowsSplitCount},
     {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
-    {kTcF16Table, &kTcF16Count}, {kTcBf16Table, &kTcBf16Count},
+    {kTcRowsTable, &kTcRowsCount}, {kTc4Table, &kTc4Count},
     {kPipeRowsIlTable, &kPipeRowsIlCount}, {kPipeRowsSplitTable, &kPipeRowsSplitCount}, {kPipe4Table, &kPipe4Count},
     {kPipeEarlyIlTable, &kPipeEarlyIlCount}, {kPipeEarlySplitTable, &kPipeEarlySplitCount},
     {kColsSplitTable, &kColsSplitCount}, {kLargeTable, &kLargeCount},

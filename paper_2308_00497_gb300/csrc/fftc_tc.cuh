@@ -1,19 +1,29 @@
-// Tensor-core radix-16 Stockham pass.
+// Radix-16 butterflies on the fifth-generation tensor cores (tcgen05, TMEM accumulators).
 //
-// Every radix-16 stage computes Y = W16 X for groups of 16 inputs, W16[t'][t] =
-// w_16^(t' t), as the real block product
-//     [Yr]   [Wr  -Wi] [Xr]
-//     [Yi] = [Wi   Wr] [Xi]
-// on the tensor cores: mma.sync m16n8k16 with FP16 or BF16 operands and FP32
-// accumulation, one MMA tile = 16 outputs x 8 butterflies. The twiddles of Eq. 1
-// (the diagonal D between stages) stay FP32 on the CUDA cores and are applied before
-// the operands are rounded. In the split modes every operand is written as hi + lo
-// (hi = rn(v), lo = rn(v - hi)) and the three products hi*hi + hi*lo + lo*hi are
-// accumulated, which recovers most of the FP32 accuracy. A leftover radix-2/4/8
-// stage (log2 L not a multiple of 4) runs in FP32 first.
+// A radix-16 stage of Eq. 1 applies DFT_16 to groups of 16 elements (the I (x) DFT_R
+// factor; Table 1 FusedIKMV / FusedMKIV). On the tensor cores the 16 x 16 complex matrix
+// W16[t'][t] = w_16^(t' t) becomes one real product per group,
+//     [yr | yi] = [xr | xi] . B,   B = [[ Wr^T, Wi^T], [-Wi^T, Wr^T]]   (32 x 32),
+// so 128 groups form one MMA of M = 128 rows (one group per row), K = 32 (16 real and 16
+// imaginary inputs) and N = 32 (16 real and 16 imaginary outputs), in two K = 16 steps.
+// The dense product replaces the sparse radix-2 network of the CUDA-core path (the
+// dense-versus-sparse contrast of Section 4).
 //
-// Data path of a CTA (C lines of length L): HBM -> shared (coalesced), every stage
-// shared -> registers -> tensor cores -> shared (two buffers), shared -> HBM.
+// Operands are FP16 or BF16 with FP32 accumulation. In the split modes every operand is
+// written as hi + lo (hi = rn(v), lo = rn(v - hi), the subtraction exact in FP32) and the
+// three products hi.hi + lo.hi + hi.lo are accumulated into the same tensor-memory tile
+// (six K = 16 steps), which recovers most of the FP32 accuracy. FP16 data are scaled by
+// 1/4 before each stage (exact) so that the growth of a radix-16 stage cannot leave the
+// FP16 range; the store scales back by 4 per stage. BF16 has FP32's exponent range.
+//
+// Data path of a group: the thread that owns the group in the CUDA-core pass kernel (16
+// elements in registers, twiddled in FP32) writes its row of A into shared memory (in
+// the no-swizzle K-major core-matrix layout, aliasing the tile's exchange buffer, which is
+// free at that point), one thread of the 128-thread group issues the MMAs and commits
+// them to an mbarrier, and every thread reads its row of D back from tensor memory
+// (tcgen05.ld 32x32b: warp w of the group owns lanes 32 (w mod 4) .. + 31) straight into
+// the registers where the CUDA-core butterfly would have left it. The pass kernel then
+// goes on unchanged: FP32 twiddles, shared-memory exchange, coalesced HBM store.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -21,308 +31,198 @@
 
 #include "fftc_device.cuh"
 #include "fftc_internal.h"
+#include "fftc_ptx.cuh"
 
 namespace fftc {
 
-enum TcPrec : int { TC_FP16 = 1, TC_BF16 = 2, TC_FP16_SPLIT = 3, TC_BF16_SPLIT = 4 };
+// tc_mode of PassParams (the fftc_precision values)
+enum TcMode : int { TC_FP16 = 1, TC_BF16 = 2, TC_FP16_SPLIT = 3, TC_BF16_SPLIT = 4 };
 
-template <int PREC>
-struct TcOps {
-    static constexpr bool BF = (PREC == TC_BF16 || PREC == TC_BF16_SPLIT);
-    static constexpr bool SPLIT = (PREC == TC_FP16_SPLIT || PREC == TC_BF16_SPLIT);
-    // FP16 operands are scaled by 1/4 per stage (exact) to keep the growth of a
-    // radix-16 stage inside the FP16 range; BF16 has the FP32 exponent range.
-    static constexpr float IN_SCALE = BF ? 1.0f : 0.25f;
-    static constexpr float OUT_SCALE = BF ? 1.0f : 4.0f;
+__host__ __device__ constexpr bool tc_is_bf16(int mode) { return mode == TC_BF16 || mode == TC_BF16_SPLIT; }
+__host__ __device__ constexpr bool tc_is_split(int mode) { return mode == TC_FP16_SPLIT || mode == TC_BF16_SPLIT; }
 
-    // pack (a, b) -> .b32 with a in the low half; *lo gets the packed remainders
-    __device__ __forceinline__ static uint32_t pack(float a, float b, uint32_t *lo) {
-        if constexpr (BF) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-            if (lo) {
-                float2 hf = __bfloat1622float2(h);
-                __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-                *lo = *reinterpret_cast<uint32_t *>(&l);
-            }
-            return *reinterpret_cast<uint32_t *>(&h);
-        } else {
-            __half2 h = __floats2half2_rn(a, b);
-            if (lo) {
-                float2 hf = __half22float2(h);
-                __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-                *lo = *reinterpret_cast<uint32_t *>(&l);
-            }
-            return *reinterpret_cast<uint32_t *>(&h);
-        }
+// Tensor-core area at the (128-byte aligned) start of dynamic shared memory:
+//   [0, 2048)     B hi: 32 rows n x 32 halves k, core-matrix layout (row group 512 B apart)
+//   [2048, 4096)  B lo (split modes)
+//   [4096, 4160)  one mbarrier per 128-thread group (MMA completion)
+//   [4160]        TMEM base address written by tcgen05.alloc
+constexpr int kTcAreaBytes = 4096 + 128;
+constexpr int kTcBLo = 2048, kTcBars = 4096, kTcTmem = 4096 + 64;
+// A rows of one 128-thread group: 16 row groups x 8 chunks of 16 bytes (hi re, hi im,
+// lo re, lo im: two chunks each) = 16 KB; row group g at g * 1024, chunk c at c * 128
+constexpr int kTcASbo = 1024, kTcAGroupBytes = 16 * kTcASbo;
+
+__device__ __forceinline__ uint32_t tc_pack2(float a, float b, bool bf) {
+    if (bf) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
     }
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
 
-    __device__ __forceinline__ static void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-        if constexpr (BF) {
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                "{%0,%1,%2,%3};\n"
-                : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-        } else {
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                "{%0,%1,%2,%3};\n"
-                : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-        }
+__device__ __forceinline__ float2 tc_unpack2(uint32_t u, bool bf) {
+    if (bf) return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u));
+    return __half22float2(*reinterpret_cast<__half2 *>(&u));
+}
+
+// hi = rn(a, b); *lo = rn(a - hi.x, b - hi.y)
+__device__ __forceinline__ uint32_t tc_split2(float a, float b, bool bf, uint32_t *lo) {
+    const uint32_t hi = tc_pack2(a, b, bf);
+    const float2 h = tc_unpack2(hi, bf);
+    *lo = tc_pack2(a - h.x, b - h.y, bf);
+    return hi;
+}
+
+__device__ __forceinline__ uint16_t tc_half_bits(float v, bool bf) {
+    if (bf) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        return *reinterpret_cast<uint16_t *>(&h);
     }
-};
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
 
-// cos and sin of 2*pi*m/16
-__device__ __forceinline__ float cos16(int m) {
+__device__ __forceinline__ float tc_half_value(uint16_t b, bool bf) {
+    if (bf) return __bfloat162float(*reinterpret_cast<__nv_bfloat16 *>(&b));
+    return __half2float(*reinterpret_cast<__half *>(&b));
+}
+
+// cos and sin of 2 pi m / 16 from the quarter-period table of fftc_device.cuh
+__device__ __forceinline__ float tc_cos16(int m) {
     m &= 15;
     const int q = m >> 2, r = m & 3;
     const float c = cos64_q(4 * r), s = cos64_q(16 - 4 * r);
     return q == 0 ? c : (q == 1 ? -s : (q == 2 ? -c : s));
 }
-__device__ __forceinline__ float sin16(int m) { return cos16(m - 4); }
+__device__ __forceinline__ float tc_sin16(int m) { return tc_cos16(m - 4); }
 
-template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
-struct TcPass {
-    using Sc = Sched<LOGL, 4, true>;  // leftover radix first, then radix-16 stages
-    using Ops = TcOps<PREC>;
-    static constexpr int L = 1 << LOGL, S = Sc::S, NT = 256, NW = NT / 32;
-    static constexpr int ROW = L / 16;            // one row per input index t of a radix-16 stage
-    static constexpr int PITCH = L + 33;          // rows padded by 2 words, lines by one more (odd)
-    static constexpr int SMEM = 2 * C * PITCH * (int)sizeof(float2);
-    static_assert(LOGL >= 7, "an MMA tile needs 8 butterflies of one line");
-    static_assert((C * L) % 128 == 0, "whole MMA tiles");
+// B[n][k] of the real form of DFT_16 (forward, w_16 = exp(-2 pi i / 16)):
+// yr_n = sum_t xr_t cos - xi_t (-sin), yi_n = sum_t xr_t (-sin) + xi_t cos, angle 2 pi n t / 16
+__device__ __forceinline__ float tc_b_value(int n, int k) {
+    const int no = n & 15, t = k & 15, m = no * t;
+    const float c = tc_cos16(m), s = tc_sin16(m);  // W = c - i s
+    if (n < 16) return k < 16 ? c : s;             // Wr, -Wi
+    return k < 16 ? -s : c;                        // Wi, Wr
+}
 
-    __device__ __forceinline__ static int rp(int a) { return (a / ROW) * (ROW + 2) + (a % ROW); }
+// TMEM columns of a CTA of nt threads: one 32-column FP32 tile per 128-thread group,
+// rounded up to a power of two >= 32 (the allocation granule)
+__host__ __device__ constexpr uint32_t tc_tmem_cols(int nt) {
+    return nt <= 128 ? 32u : (nt <= 256 ? 64u : (nt <= 512 ? 128u : 256u));
+}
 
-    __device__ __forceinline__ static int64_t line_base(const PassParams &p, int64_t g, int64_t tr, int64_t line) {
-        return (g >> p.log_lpt) * tr + (g & ((int64_t(1) << p.log_lpt) - 1)) * line;
-    }
+template <int NT>
+struct TcUnit {
+    static_assert(NT % 128 == 0 && NT <= 1024, "whole 128-thread MMA groups");
+    static constexpr int NWG = NT / 128;
+    static constexpr uint32_t COLS = tc_tmem_cols(NT);
 
-    // Element (c, a) of the tile handled by iteration `it` of thread `tid`. Row-contiguous
-    // kinds walk a line with consecutive threads; the column kind walks C lines.
-    static constexpr int ITER = C * L / NT;
-    static_assert(ITER * NT == C * L, "whole tiles per thread");
-    template <bool TAU>
-    __device__ __forceinline__ static void coord(int tid, int it, int &c, int &a) {
-        const int i = tid + it * NT;
-        if constexpr (TAU) {
-            c = i >> LOGL;
-            a = i & (L - 1);
-        } else {
-            c = i % C;
-            a = i / C;
+    // every thread: DFT matrices into shared memory, mbarriers, TMEM columns
+    __device__ static void setup(const PassParams &p, unsigned char *area) {
+        const bool bf = tc_is_bf16(p.tc_mode);
+        for (int i = threadIdx.x; i < 32 * 32; i += NT) {
+            const int n = i >> 5, k = i & 31;
+            const float v = tc_b_value(n, k);
+            const uint16_t hi = tc_half_bits(v, bf);
+            const uint16_t lo = tc_half_bits(v - tc_half_value(hi, bf), bf);
+            const int off = (n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+            *reinterpret_cast<uint16_t *>(area + off) = hi;
+            *reinterpret_cast<uint16_t *>(area + kTcBLo + off) = lo;
         }
-    }
-
-    // HBM -> shared, all loads of a thread issued before its first store
-    __device__ static void copy_in(const PassParams &p, float2 *buf, int64_t g0) {
-        constexpr bool TAU = (KIND != KIND_COLS);
-        constexpr int CH = ITER < 16 ? ITER : 16;  // loads in flight per thread
-        const int es = (int)p.in_elem;
-#pragma unroll
-        for (int b0 = 0; b0 < ITER; b0 += CH) {
-            float2 x[CH];
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                int c, a;
-                coord<TAU>(threadIdx.x, b0 + u, c, a);
-                const int64_t g = g0 + c;
-                x[u] = make_float2(0.f, 0.f);
-                if (g < p.total_lines) {
-                    const int64_t off = line_base(p, g, p.in_tr, p.in_line) + (int64_t)a * es;
-                    if constexpr (LIN == LAYOUT_IL) {
-                        if constexpr (KIND == KIND_ROWST) x[u] = __ldcg(reinterpret_cast<const float2 *>(p.in) + off);
-                        else x[u] = __ldcs(reinterpret_cast<const float2 *>(p.in) + off);
-                    } else {
-                        x[u].x = __ldcs(p.in + off);
-                        x[u].y = __ldcs(p.in + p.in_plane + off);
-                    }
-                    if (p.conj_in) x[u].y = -x[u].y;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                int c, a;
-                coord<TAU>(threadIdx.x, b0 + u, c, a);
-                buf[c * PITCH + rp(a)] = x[u];
-            }
+        uint64_t *bars = reinterpret_cast<uint64_t *>(area + kTcBars);
+        if (threadIdx.x == 0) {
+            for (int g = 0; g < NWG; ++g) mbar_init(bars + g, 1);
+            fence_mbar_init();
         }
-    }
-
-    // shared -> HBM (with the inter-pass twiddle for the column kind)
-    __device__ static void copy_out(const PassParams &p, const float2 *buf, int64_t g0) {
-        constexpr bool TAU = (KIND == KIND_ROWS);
-        const int es = (int)p.out_elem;
-#pragma unroll
-        for (int it = 0; it < ITER; ++it) {
-            int c, a;
-            coord<TAU>(threadIdx.x, it, c, a);
-            const int64_t g = g0 + c;
-            if (g >= p.total_lines) continue;
-            float2 x = buf[c * PITCH + rp(a)];
-            const int l = (int)(g & ((int64_t(1) << p.log_lpt) - 1));
-            if constexpr (KIND == KIND_COLS) {
-                if (p.tw2_full) {
-                    x = cmul(x, __ldg(p.tw2_full + l * (int)p.out_line + a * es));
-                } else {
-                    const int m = (l * a) & ((1 << p.log_n2) - 1);
-                    x = cmul(x, cmul(__ldg(p.tw2_lo + (m & ((1 << p.tw2_lo_bits) - 1))),
-                                     __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
-                }
-            }
-            if (p.conj_out) x.y = -x.y;
-            const int64_t off = line_base(p, g, p.out_tr, p.out_line) + (int64_t)a * es;
-            if constexpr (KIND == KIND_COLS) {
-                __stcg(reinterpret_cast<float2 *>(p.out) + off, x);
-            } else if constexpr (LOUT == LAYOUT_IL) {
-                __stcs(reinterpret_cast<float2 *>(p.out) + off, x);
-            } else {
-                __stcs(p.out + off, x.x);
-                __stcs(p.out + p.out_plane + off, x.y);
-            }
-        }
-    }
-
-    // FP32 leftover stage (first stage, Ns = 1, radix R < 16)
-    template <int R>
-    __device__ static void small_stage(const float2 *src, float2 *dst) {
-        for (int i = threadIdx.x; i < C * (L / R); i += NT) {
-            const int c = i / (L / R), j = i % (L / R);
-            float2 v[R];
-#pragma unroll
-            for (int t = 0; t < R; ++t) v[t] = src[c * PITCH + rp(j + t * (L / R))];
-            dft<R>(v);
-#pragma unroll
-            for (int t = 0; t < R; ++t) dst[c * PITCH + rp(j * R + t)] = v[t];
-        }
-    }
-
-    // one radix-16 stage on the tensor cores
-    template <int LNS>
-    __device__ static void tc_stage(const PassParams &p, const float2 *src, float2 *dst, const uint32_t (&wr)[4],
-                                    const uint32_t (&wi)[4], const uint32_t (&nwi)[4], const uint32_t (&wrl)[4],
-                                    const uint32_t (&wil)[4], const uint32_t (&nwil)[4], const float2 *tw) {
-        constexpr int NS = 1 << LNS;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int g = lane >> 2, tig = lane & 3;
-        const int tt[4] = {2 * tig, 2 * tig + 1, 2 * tig + 8, 2 * tig + 9};
-        constexpr int GROUPS = C * L / 128;
-        for (int grp = warp; grp < GROUPS; grp += NW) {
-            const int c = grp / (L / 128), j0 = (grp % (L / 128)) * 8;
-            const float2 *s = src + c * PITCH;
-            const int j = j0 + g;
-            float2 x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = s[j + tt[u] * (ROW + 2)];  // = rp(j + t ROW), j < ROW
-            if constexpr (NS > 1) {
-                const int k = j & (NS - 1);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (tt[u] > 0) x[u] = cmul(x[u], __ldg(tw + (tt[u] - 1) * NS + k));
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                x[u].x *= Ops::IN_SCALE;
-                x[u].y *= Ops::IN_SCALE;
-            }
-            uint32_t brl[2], bil[2];
-            const uint32_t br0 = Ops::pack(x[0].x, x[1].x, Ops::SPLIT ? &brl[0] : nullptr);
-            const uint32_t br1 = Ops::pack(x[2].x, x[3].x, Ops::SPLIT ? &brl[1] : nullptr);
-            const uint32_t bi0 = Ops::pack(x[0].y, x[1].y, Ops::SPLIT ? &bil[0] : nullptr);
-            const uint32_t bi1 = Ops::pack(x[2].y, x[3].y, Ops::SPLIT ? &bil[1] : nullptr);
-            float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
-            Ops::mma(yr, wr, br0, br1);    // Wr Xr
-            Ops::mma(yr, nwi, bi0, bi1);   // - Wi Xi
-            Ops::mma(yi, wi, br0, br1);    // Wi Xr
-            Ops::mma(yi, wr, bi0, bi1);    // Wr Xi
-            if constexpr (Ops::SPLIT) {
-                Ops::mma(yr, wr, brl[0], brl[1]);
-                Ops::mma(yr, nwi, bil[0], bil[1]);
-                Ops::mma(yi, wi, brl[0], brl[1]);
-                Ops::mma(yi, wr, bil[0], bil[1]);
-                Ops::mma(yr, wrl, br0, br1);
-                Ops::mma(yr, nwil, bi0, bi1);
-                Ops::mma(yi, wil, br0, br1);
-                Ops::mma(yi, wrl, bi0, bi1);
-            }
-            // d[0]: (t' = g, butterfly 2 tig), d[1]: (g, 2 tig + 1), d[2]: (g + 8, 2 tig), d[3]: (g + 8, 2 tig + 1)
-            float2 *d = dst + c * PITCH;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int jj = j0 + 2 * tig + (r & 1);
-                const int tp = g + ((r & 2) ? 8 : 0);
-                const int pos = ((jj >> LNS) << (LNS + 4)) + (jj & (NS - 1)) + tp * NS;
-                d[rp(pos)] = make_float2(yr[r] * Ops::OUT_SCALE, yi[r] * Ops::OUT_SCALE);
-            }
-        }
-    }
-
-    template <int s>
-    __device__ static void stages(const PassParams &p, float2 *a, float2 *b, const uint32_t (&wr)[4],
-                                  const uint32_t (&wi)[4], const uint32_t (&nwi)[4], const uint32_t (&wrl)[4],
-                                  const uint32_t (&wil)[4], const uint32_t (&nwil)[4]) {
-        constexpr int LR = Sc::lr(s), LNS = Sc::lns(s);
-        if constexpr (LR < 4) {
-            small_stage<1 << LR>(a, b);
-        } else {
-            tc_stage<LNS>(p, a, b, wr, wi, nwi, wrl, wil, nwil, p.tw + Sc::tw_off(s));
-        }
+        if (threadIdx.x < 32) tmem_alloc(reinterpret_cast<uint32_t *>(area + kTcTmem), COLS);
+        fence_proxy_async_smem();  // B is read by the tensor cores
+        tc_fence_before();
         __syncthreads();
-        if constexpr (s + 1 < S) stages<s + 1>(p, b, a, wr, wi, nwi, wrl, wil, nwil);
+        tc_fence_after();
     }
 
-    __device__ static void run(const PassParams &p) {
-        extern __shared__ float2 sm_tc[];
-        float2 *a = sm_tc, *b = sm_tc + C * PITCH;
-        // W16 fragments (A operand, rows t' = g, g + 8; columns t = 2 tig (+1), 2 tig + 8 (+9))
-        const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
-        uint32_t wr[4], wi[4], nwi[4], wrl[4] = {0, 0, 0, 0}, wil[4] = {0, 0, 0, 0}, nwil[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int row = g + ((r & 1) ? 8 : 0), col = 2 * tig + ((r & 2) ? 8 : 0);
-            const int m0 = (row * col) & 15, m1 = (row * (col + 1)) & 15;
-            // W = cos - i sin (forward): Wr = cos, Wi = -sin
-            wr[r] = Ops::pack(cos16(m0), cos16(m1), Ops::SPLIT ? &wrl[r] : nullptr);
-            wi[r] = Ops::pack(-sin16(m0), -sin16(m1), Ops::SPLIT ? &wil[r] : nullptr);
-            nwi[r] = Ops::pack(sin16(m0), sin16(m1), Ops::SPLIT ? &nwil[r] : nullptr);
-        }
-        const int64_t g0 = (int64_t)blockIdx.x * C;
-        copy_in(p, a, g0);
+    __device__ static void teardown(unsigned char *area) {
+        tc_fence_before();
         __syncthreads();
-        stages<0>(p, a, b, wr, wi, nwi, wrl, wil, nwil);
-        copy_out(p, (S % 2) ? b : a, g0);
+        if (threadIdx.x < 32) tmem_free(*reinterpret_cast<volatile uint32_t *>(area + kTcTmem), COLS);
+    }
+
+    // v = DFT_16 v for the thread's group (forward), on the tensor cores. `a_smem` is the
+    // shared-memory address of the A rows (NT * 128 bytes, free to overwrite); `phase` the
+    // parity of this use of the group's mbarrier. The caller synchronises the CTA before
+    // (every read of the aliased buffer done) and after (every group's MMA done).
+    __device__ __forceinline__ static void dft16(const PassParams &p, float2 (&v)[16], unsigned char *area,
+                                                 uint32_t a_smem, uint32_t phase) {
+        const int mode = p.tc_mode;
+        const bool bf = tc_is_bf16(mode), split = tc_is_split(mode);
+        const int tid = threadIdx.x, wg = tid >> 7, m = tid & 127;
+        if (!bf) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                v[t].x *= 0.25f;
+                v[t].y *= 0.25f;
+            }
+        }
+        const uint32_t aw = a_smem + wg * kTcAGroupBytes;
+        const uint32_t row = aw + (m >> 3) * kTcASbo + (m & 7) * 16;
+        if (split) {
+            uint32_t hr[8], hi_[8], lr[8], li[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hr[j] = tc_split2(v[2 * j].x, v[2 * j + 1].x, bf, &lr[j]);
+                hi_[j] = tc_split2(v[2 * j].y, v[2 * j + 1].y, bf, &li[j]);
+            }
+            st_shared_v4(row + 0 * 128, hr[0], hr[1], hr[2], hr[3]);
+            st_shared_v4(row + 1 * 128, hr[4], hr[5], hr[6], hr[7]);
+            st_shared_v4(row + 2 * 128, hi_[0], hi_[1], hi_[2], hi_[3]);
+            st_shared_v4(row + 3 * 128, hi_[4], hi_[5], hi_[6], hi_[7]);
+            st_shared_v4(row + 4 * 128, lr[0], lr[1], lr[2], lr[3]);
+            st_shared_v4(row + 5 * 128, lr[4], lr[5], lr[6], lr[7]);
+            st_shared_v4(row + 6 * 128, li[0], li[1], li[2], li[3]);
+            st_shared_v4(row + 7 * 128, li[4], li[5], li[6], li[7]);
+        } else {
+            uint32_t hr[8], hi_[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hr[j] = tc_pack2(v[2 * j].x, v[2 * j + 1].x, bf);
+                hi_[j] = tc_pack2(v[2 * j].y, v[2 * j + 1].y, bf);
+            }
+            st_shared_v4(row + 0 * 128, hr[0], hr[1], hr[2], hr[3]);
+            st_shared_v4(row + 1 * 128, hr[4], hr[5], hr[6], hr[7]);
+            st_shared_v4(row + 2 * 128, hi_[0], hi_[1], hi_[2], hi_[3]);
+            st_shared_v4(row + 3 * 128, hi_[4], hi_[5], hi_[6], hi_[7]);
+        }
+        fence_proxy_async_smem();  // the rows are read by the tensor cores
+        named_bar(1 + wg, 128);
+        uint64_t *bar = reinterpret_cast<uint64_t *>(area + kTcBars) + wg;
+        const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(area + kTcTmem);
+        if (m == 0) {
+            tc_fence_after();
+            const uint32_t d = tmem + 32 * wg;  // columns of this group's 128 x 32 FP32 tile
+            const uint32_t idesc = umma_idesc_f16(bf, 128, 32);
+            const uint32_t bhi = smem_u32(area), blo = bhi + kTcBLo;
+            // K = 16 steps: (A chunks, B chunks) = (re, re-rows of B), (im, im-rows of B)
+            umma_f16(d, umma_desc(aw, 128, kTcASbo), umma_desc(bhi, 128, 512), idesc, 0);
+            umma_f16(d, umma_desc(aw + 256, 128, kTcASbo), umma_desc(bhi + 256, 128, 512), idesc, 1);
+            if (split) {
+                umma_f16(d, umma_desc(aw + 512, 128, kTcASbo), umma_desc(bhi, 128, 512), idesc, 1);        // lo.hi
+                umma_f16(d, umma_desc(aw + 768, 128, kTcASbo), umma_desc(bhi + 256, 128, 512), idesc, 1);
+                umma_f16(d, umma_desc(aw, 128, kTcASbo), umma_desc(blo, 128, 512), idesc, 1);              // hi.lo
+                umma_f16(d, umma_desc(aw + 256, 128, kTcASbo), umma_desc(blo + 256, 128, 512), idesc, 1);
+            }
+            umma_commit(bar);
+        }
+        const long long limit = p.spin_limit > 0 ? (long long)p.spin_limit : kMbarSpinLimit;
+        if (!mbar_wait_sleepy(bar, phase, limit) && m == 0 && p.err) atomicExch(p.err, 3);
+        tc_fence_after();
+        __syncwarp();  // tcgen05.ld is warp-collective
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 32 * wg, r);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] = make_float2(__uint_as_float(r[t]), __uint_as_float(r[16 + t]));
+        tc_fence_before();
     }
 };
-
-template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
-__global__ void __launch_bounds__(256) k_tc(const __grid_constant__ PassParams p) {
-    TcPass<LOGL, C, KIND, LIN, LOUT, PREC>::run(p);
-}
-
-template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
-cudaError_t launch_tc(const PassParams &p, cudaStream_t st) {
-    using P = TcPass<LOGL, C, KIND, LIN, LOUT, PREC>;
-    const int64_t blocks = (p.total_lines + C - 1) / C;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    k_tc<LOGL, C, KIND, LIN, LOUT, PREC><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
-    return cudaGetLastError();
-}
-
-template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
-cudaError_t prepare_tc() {
-    using P = TcPass<LOGL, C, KIND, LIN, LOUT, PREC>;
-    if (P::SMEM <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_tc<LOGL, C, KIND, LIN, LOUT, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                P::SMEM);
-}
-
-template <int LOGL, int C, int KIND, int LIN, int LOUT, int PREC>
-constexpr KernelEntry tc_entry() {
-    using P = TcPass<LOGL, C, KIND, LIN, LOUT, PREC>;
-    return KernelEntry{KIND,   LOGL,   4, C, LIN, LOUT, P::NT, P::SMEM, &launch_tc<LOGL, C, KIND, LIN, LOUT, PREC>,
-                       &prepare_tc<LOGL, C, KIND, LIN, LOUT, PREC>, PREC, 0, 0};
-}
 
 }  // namespace fftc

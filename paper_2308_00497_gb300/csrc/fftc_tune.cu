@@ -1,13 +1,15 @@
-// Measurement-driven kernel choice for a plan (FFTW's "measure" planning, the runtime
-// decomposition search the paper leaves to future work, Section 6): every compiled kernel
-// that can run a pass of this plan is timed on scratch buffers of the plan's size and the
-// fastest is kept.
+// Measurement-driven planning (FFTW's "measure" mode, the runtime search over
+// decompositions that the paper leaves to future work, Section 6): candidate plans are
+// timed on scratch buffers of the plan's size and the fastest is kept.
 //   single pass: every registered rows kernel for (n, layout): plain, bulk-copy fed with
 //                each landing-buffer count and refill point, each elements-per-thread
+//                (the radix schedule of the line: radix 2^loge stages, remainder last)
 //                and tile height;
-//   four-step:   for the plan's split n = M K, every column kernel for pass 1 (plain with
-//                and without the L2 prefetch, tensor-map fed; compile-time or runtime
-//                stride) and every transposed-row kernel for pass 2, timed pass by pass.
+//   four-step:   every split n = M K of Eq. 1 at the memory level with compiled kernels
+//                for both passes, and for each split every column kernel for pass 1
+//                (plain with and without the L2 prefetch, tensor-map fed; compile-time
+//                or runtime stride; each radix schedule) and every transposed-row kernel
+//                for pass 2, timed pass by pass; the split with the smallest sum wins.
 // Choices are cached per (n, batch, layout, direction) for the process.
 #include <cuda_runtime.h>
 
@@ -23,6 +25,7 @@ namespace fftc {
 namespace {
 
 struct Choice {
+    int logm = 0;  // four-step split n = 2^logm * 2^(logn - logm) (unused for one pass)
     const KernelEntry *k1 = nullptr, *k2 = nullptr;
     int pf1 = 0;
 };
@@ -86,6 +89,18 @@ fftc_status apply(fftc_plan_s *p, const Choice &c, std::map<std::pair<int, int>,
     if (p->npasses == 2 && !tables_for(p, tabs, c.k2->logl, c.k2->loge, &t1)) return FFTC_ERR_ALLOC;
     if (c.k1->prepare() != cudaSuccess || (p->npasses == 2 && c.k2->prepare() != cudaSuccess)) return FFTC_ERR_CUDA;
     PassPlan &p0 = p->pass[0];
+    if (p->npasses == 2 && c.logm != p0.logl) {  // another split: its diagonal and pass shapes
+        if (p->tw2_full) {
+            float2 *d = nullptr;
+            fftc_status st = upload_full_diagonal(p, c.logm, &d);
+            if (st != FFTC_OK) return st;
+            plan_release(p, p->tw2_full);
+            p->tw2_full = d;
+        }
+        four_step_params(p, c.logm, p0.base, p->pass[1].base);
+        p0.logl = c.logm;
+        p->pass[1].logl = p->logn - c.logm;
+    }
     p0.k = c.k1;
     p0.loge = c.k1->loge;
     p0.lines = c.k1->lines;
@@ -103,10 +118,69 @@ fftc_status apply(fftc_plan_s *p, const Choice &c, std::map<std::pair<int, int>,
     return FFTC_OK;
 }
 
+// fastest pass-1 and pass-2 kernels of one four-step split, with their summed time
+float time_split(fftc_plan_s *p, int logm, const float2 *diag, Scratch &s, int reps,
+                 std::map<std::pair<int, int>, const float2 *> &tabs, Choice *out, fftc_status *err) {
+    const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
+    const int logk = p->logn - logm, inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    PassParams a0, b0;
+    four_step_params(p, logm, a0, b0);
+    a0.tw2_full = diag;
+    float t1 = 1e30f, t2 = 1e30f;
+    Choice c;
+    c.logm = logm;
+    for (int i = 0; i < kernel_count(); ++i) {
+        const KernelEntry *e = kernel_at(i);
+        if (e->prec != 0) continue;
+        if (e->kind == KIND_COLS && e->logl == logm && e->lin == lay && e->lout == LAYOUT_IL &&
+            (e->logx == 0 || e->logx == logk)) {
+            for (int pf : {0, -1}) {
+                if (pf && e->pipe) continue;  // the prefetch belongs to the plain kernel
+                PassParams a = a0;
+                if (!tables_for(p, tabs, e->logl, e->loge, &a.tw)) {
+                    *err = FFTC_ERR_ALLOC;
+                    return -1.f;
+                }
+                a.pf_tiles = pf;
+                a.in = (const float *)s.in;
+                a.out = (float *)p->workspace;
+                a.conj_in = inv;
+                const float t = time_launch(e, a, s, reps);
+                if (t > 0.f && t < t1) {
+                    t1 = t;
+                    c.k1 = e;
+                    c.pf1 = pf;
+                }
+            }
+        } else if (e->kind == KIND_ROWST && e->logl == logk && e->lin == LAYOUT_IL && e->lout == lay &&
+                   (e->logx == 0 || e->logx == logm)) {
+            PassParams b = b0;
+            if (!tables_for(p, tabs, e->logl, e->loge, &b.tw)) {
+                *err = FFTC_ERR_ALLOC;
+                return -1.f;
+            }
+            b.in = (const float *)p->workspace;
+            b.out = (float *)s.out;
+            b.conj_out = inv;
+            const float t = time_launch(e, b, s, reps);
+            if (t > 0.f && t < t2) {
+                t2 = t;
+                c.k2 = e;
+            }
+        }
+    }
+    if (!c.k1 || !c.k2) return -1.f;
+    *out = c;
+    return t1 + t2;
+}
+
 }  // namespace
 
 fftc_status plan_tune(fftc_plan_s *p, int reps) {
-    if (p->uneven || p->fs || p->mixed || p->nd || p->precision != FFTC_FP32 || p->batch == 0) return FFTC_OK;
+    if (p->batch == 0) return FFTC_OK;
+    if (p->mixed) return mixed_tune(p, reps);
+    if (p->nd) return nd_tune(p, reps);
+    if (p->uneven || p->fs || p->precision != FFTC_FP32) return FFTC_OK;
     if (reps < 1) reps = 1;
     const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
     const auto key = std::make_tuple(p->n, p->batch, (int)p->layout, (int)p->direction);
@@ -124,16 +198,17 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
         return FFTC_ERR_CUDA;
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
     Choice best;
+    best.logm = p->pass[0].logl;
     best.k1 = p->pass[0].k;
     best.k2 = p->npasses == 2 ? p->pass[1].k : nullptr;
     best.pf1 = p->pass[0].base.pf_tiles;
-    float t1 = 1e30f, t2 = 1e30f;
     const PassPlan &p0 = p->pass[0];
-    for (int i = 0; i < kernel_count(); ++i) {
-        const KernelEntry *e = kernel_at(i);
-        if (e->prec != 0) continue;
-        if (p->npasses == 1) {
-            if (e->kind != KIND_ROWS || e->logl != p0.logl || e->lin != lay || e->lout != lay) continue;
+    if (p->npasses == 1) {
+        float t1 = 1e30f;
+        for (int i = 0; i < kernel_count(); ++i) {
+            const KernelEntry *e = kernel_at(i);
+            if (e->prec != 0 || e->kind != KIND_ROWS || e->logl != p0.logl || e->lin != lay || e->lout != lay)
+                continue;
             PassParams a = p0.base;
             if (!tables_for(p, tabs, e->logl, e->loge, &a.tw)) return FFTC_ERR_ALLOC;
             a.in = (const float *)s.in;
@@ -144,39 +219,30 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
                 t1 = t;
                 best.k1 = e;
             }
-            continue;
         }
-        const PassPlan &p1 = p->pass[1];
-        if (e->kind == KIND_COLS && e->logl == p0.logl && e->lin == lay && e->lout == LAYOUT_IL &&
-            (e->logx == 0 || e->logx == p1.logl)) {
-            for (int pf : {0, -1}) {
-                if (pf && e->pipe) continue;  // the prefetch belongs to the plain kernel
-                PassParams a = p0.base;
-                if (!tables_for(p, tabs, e->logl, e->loge, &a.tw)) return FFTC_ERR_ALLOC;
-                a.pf_tiles = pf;
-                a.in = (const float *)s.in;
-                a.out = (float *)p->workspace;
-                a.conj_in = inv;
-                a.conj_out = 0;
-                const float t = time_launch(e, a, s, reps);
-                if (t > 0.f && t < t1) {
-                    t1 = t;
-                    best.k1 = e;
-                    best.pf1 = pf;
+    } else {
+        // every split M K whose factors have compiled kernels (columns 2^6..2^12, rows 2^7..2^12)
+        float tbest = 1e30f;
+        for (int logm = 6; logm <= 12; ++logm) {
+            const int logk = p->logn - logm;
+            if (logk < 7 || logk > 12) continue;
+            float2 *diag = nullptr;
+            if (p->tw2_full) {  // the whole diagonal of this split (n <= 2^20)
+                if (logm == p0.logl) {
+                    diag = p->tw2_full;
+                } else {
+                    fftc_status st = upload_full_diagonal(p, logm, &diag);
+                    if (st != FFTC_OK) return st;
                 }
             }
-        } else if (e->kind == KIND_ROWST && e->logl == p1.logl && e->lin == LAYOUT_IL && e->lout == lay &&
-                   (e->logx == 0 || e->logx == p0.logl)) {
-            PassParams b = p1.base;
-            if (!tables_for(p, tabs, e->logl, e->loge, &b.tw)) return FFTC_ERR_ALLOC;
-            b.in = (const float *)p->workspace;
-            b.out = (float *)s.out;
-            b.conj_in = 0;
-            b.conj_out = inv;
-            const float t = time_launch(e, b, s, reps);
-            if (t > 0.f && t < t2) {
-                t2 = t;
-                best.k2 = e;
+            Choice c;
+            fftc_status err = FFTC_OK;
+            const float t = time_split(p, logm, diag, s, reps, tabs, &c, &err);
+            if (diag && diag != p->tw2_full) plan_release(p, diag);
+            if (err != FFTC_OK) return err;
+            if (t > 0.f && t < tbest) {
+                tbest = t;
+                best = c;
             }
         }
     }

@@ -265,11 +265,71 @@ def test_tuned_plan_matches_oracle(e, layout):
     B = max(3, (1 << 22) // n)
     x = si.uniform_complex(B, n, seed=e + 40)
     inverse = e % 2 == 1
+    splits = set()
     for _ in range(2):
         p = fc.Plan(n, B, layout, inverse).tune(3)
-        y = from_device(p.execute(to_device(x, layout)), layout)
+        xd = to_device(x, layout)
+        y1 = p.execute(xd)
+        y2 = p.execute(xd)  # replay of the tuned plan: bit-identical
         torch.cuda.synchronize()
         p.check()
+        assert torch.equal(y1, y2)
+        y = from_device(y1, layout)
         rows = np.array([0, B // 2, B - 1])
         ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
         assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
+        m, k = p.split()
+        passes, radices = p.info()
+        assert m * k == n and int(np.prod(radices)) == n
+        if passes == 2:  # the radices of pass 1 multiply to the tuned M
+            acc, i = 1, 0
+            while acc < m:
+                acc *= radices[i]
+                i += 1
+            assert acc == m
+        splits.add((m, k))
+    assert len(splits) == 1  # the second plan reuses the cached choice
+
+
+def _timeout_then_recover(monkeypatch, n, B, layout, env):
+    """Plan built with a test hook that makes every bounded device wait run out and a tiny
+    poll limit: the kernel gives up, sets the plan's error word and returns, so
+    fftc_plan_check reports FFTC_ERR_TIMEOUT (once: the word is cleared). A plan built
+    afterwards without the hook still runs and matches the oracle."""
+    import paper_2308_00497_gb300 as fc
+    from paper_2308_00497_gb300 import _native as nat
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    monkeypatch.setenv("FFTC_TEST_UNREACHABLE_WAIT", "1")
+    monkeypatch.setenv("FFTC_SPIN_LIMIT", "200")
+    p = fc.Plan(n, B, layout)
+    x = to_device(np.zeros((B, n), np.complex64), layout)
+    p.execute(x)
+    with pytest.raises(nat.FftcError) as ei:
+        p.check()
+    assert ei.value.status == nat.ERR_TIMEOUT
+    p.check()
+    p.close()
+    monkeypatch.delenv("FFTC_TEST_UNREACHABLE_WAIT")
+    monkeypatch.delenv("FFTC_SPIN_LIMIT")
+    xh = si.uniform_complex(B, n, seed=77)
+    q = fc.Plan(n, B, layout)
+    y = from_device(q.execute(to_device(xh, layout)), layout)
+    q.check()
+    err = rel_l2_rows(y, oracle.fft(xh.astype(np.complex128)))
+    assert err.max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e,layout", [(12, "interleaved"), (14, "split"), (17, "interleaved"), (18, "split")])
+def test_pipelined_mbarrier_wait_reports_timeout(monkeypatch, e, layout):
+    """The bulk-copy fed kernels (single pass at 2^12, 2^14; four-step passes fed by bulk
+    copies or tensor-map boxes at 2^17, 2^18) wait on their landing-buffer mbarriers with a
+    poll limit; with the hook no copy is issued, so each wait runs out."""
+    _timeout_then_recover(monkeypatch, 1 << e, 3, layout, {})
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_l2_resident_counter_wait_reports_timeout(monkeypatch, layout):
+    """The L2-resident four-step spins on per-group counters; with the hook every awaited
+    count is out of reach, so each spin runs out after its poll limit."""
+    _timeout_then_recover(monkeypatch, 1 << 16, 8, layout, {"FFTC_L2_RESIDENT": "1"})

@@ -128,3 +128,29 @@ def test_in_place_batch_one_and_empty(n):
     e = fc.Plan(n, 0)
     e.execute(torch.empty((0, n), dtype=torch.complex64, device="cuda"))
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("n,layout", [(59049, "interleaved"), (100000, "split"), (1000000, "interleaved")])
+def test_tuned_split_search(n, layout):
+    """Measure-mode planning of a two-pass mixed length times the divisor splits n = M K
+    closest to sqrt(n) and keeps the fastest: the plan then reports a split with M K = n,
+    matches the oracle, replays bit-identically, and a second plan reuses the choice."""
+    import paper_2308_00497_gb300 as fc
+    B = 4
+    x = si.uniform_complex(B, n, seed=n % 997)
+    ref = oracle.fft(x[[0, B - 1]].astype(np.complex128))
+    splits = set()
+    for _ in range(2):
+        p = fc.Plan(n, B, layout, False).tune(2)
+        m, k = p.split()
+        assert m * k == n and 1 < m < n
+        xd = to_device(x, layout)
+        a = p.execute(xd)
+        b = p.execute(xd)
+        torch.cuda.synchronize()
+        p.check()
+        assert torch.equal(a, b)
+        y = from_device(a, layout)
+        assert rel_l2_rows(y[[0, B - 1]], ref).max() <= tol_fp32(n)
+        splits.add((m, k))
+    assert len(splits) == 1

@@ -96,3 +96,20 @@ def test_fp64_arrays(dims, layout):
     y = _from(fc.fftn(t, len(dims), layout=layout), layout)
     ref = oracle.fftn(x, len(dims))
     assert _rel(y, ref).max() <= 1e-14 * math.log2(N)
+
+
+@pytest.mark.parametrize("dims,layout", [((256, 256), "interleaved"), ((64, 64, 64), "split"), ((96, 100), "split")])
+def test_tuned_nd_plan(dims, layout):
+    """Measure-mode planning of a multidimensional plan tunes its last-axis 1D plan and picks,
+    for every strided power-of-two axis, the compiled column pass or the runtime-radix pass;
+    the result stays within tolerance of the oracle."""
+    import paper_2308_00497_gb300 as fc
+    N = int(np.prod(dims))
+    B = 2
+    x = si.uniform_complex(B, N, seed=N % 991).reshape((B,) + dims)
+    p = fc.NdPlan(dims, B, layout, False).tune(2)
+    y = _from(p.execute(_to(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    ref = oracle.fftn(x.astype(np.complex128), len(dims), False)
+    assert _rel(y, ref).max() <= tol_fp32(N)

@@ -45,7 +45,7 @@ def _run(x, layout, inverse, mode):
     return from_device(y, layout)
 
 
-SIZES = [7, 8, 10, 11, 12, 13, 14, 15, 16]
+SIZES = list(range(7, 17))
 
 
 @pytest.mark.parametrize("mode", list(U))
@@ -59,13 +59,32 @@ def test_tc_modes_within_bound(mode, e):
     assert err <= bound(mode, n), (mode, n, float(err), bound(mode, n))
 
 
-@pytest.mark.parametrize("mode", ["fp16_tc_split", "bf16_tc"])
-@pytest.mark.parametrize("e", [9, 14])
-def test_tc_split_layout_and_inverse(mode, e):
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("mode", list(U))
+@pytest.mark.parametrize("e", [7, 9, 12, 13, 14, 15, 16])
+def test_tc_layouts_and_directions(layout, inverse, mode, e):
+    """Every kernel kind (plain tiles, bulk-copy fed tiles with one or two landing buffers,
+    both four-step passes with plain or tensor-map fed columns) in both layouts and
+    directions; batches that leave the last tile ragged."""
     n = 1 << e
-    x = si.gaussian_complex(6, n, seed=400 + e)
-    ref = oracle.fft(x.astype(np.complex128), inverse=True)
-    err = rel_l2_rows(_run(x, "split", True, mode), ref).max()
+    B = {7: 45, 9: 11, 12: 5}.get(e, 3)
+    x = si.gaussian_complex(B, n, seed=400 + e)
+    ref = oracle.fft(x.astype(np.complex128), inverse=inverse)
+    err = rel_l2_rows(_run(x, layout, inverse, mode), ref).max()
+    assert err <= bound(mode, n), (mode, n, float(err))
+
+
+@pytest.mark.parametrize("mode", list(U))
+@pytest.mark.parametrize("e", [8, 13, 16])
+def test_tc_pure_tone(mode, e):
+    """A unit tone at bin k0 maps to n at k0 and (up to the mode's error) zero elsewhere."""
+    n = 1 << e
+    x, k0 = si.tones(4, n, seed=600 + e)
+    y = _run(x, "interleaved", False, mode)
+    want = np.zeros((4, n), np.complex128)
+    want[np.arange(4), k0] = n
+    err = rel_l2_rows(y, want).max()
     assert err <= bound(mode, n), (mode, n, float(err))
 
 
@@ -80,15 +99,22 @@ def test_split_recovers_accuracy(e):
     assert err["bf16_tc"] > err["fp16_tc"]  # fewer mantissa bits, larger error
 
 
-def test_tc_determinism_and_rejects_small_n():
+@pytest.mark.parametrize("e", [12, 14, 16])
+def test_tc_determinism_and_rejects_small_n(e):
+    """Bit-identical output on repeats and on another stream (the MMA accumulation order
+    is fixed by the plan)."""
     import paper_2308_00497_gb300 as fc
     from paper_2308_00497_gb300 import _native as nat
-    x = to_device(si.gaussian_complex(64, 4096, seed=1), "interleaved")
-    p = fc.Plan(4096, 64, precision="fp16_tc_split")
+    x = to_device(si.gaussian_complex(8, 1 << e, seed=1), "interleaved")
+    p = fc.Plan(1 << e, 8, precision="fp16_tc_split")
     a = p.execute(x)
     b = p.execute(x)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        c = p.execute(x, stream=s)
     torch.cuda.synchronize()
     assert torch.equal(a.view(torch.float32), b.view(torch.float32))
+    assert torch.equal(a.view(torch.float32), c.view(torch.float32))
     with pytest.raises(nat.FftcError):
         fc.Plan(64, 4, precision="fp16_tc")
 
