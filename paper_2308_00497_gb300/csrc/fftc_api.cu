@@ -265,7 +265,7 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
     }
     if (plan->mixed) cnt = mixed_radix_list(plan, tmp, 32);
     if (plan->nd) cnt = 0;  // several 1D factorisations: the pass count alone is reported
-    const int nsched = plan->fs ? 2 : plan->npasses;
+    const int nsched = (plan->fs || plan->cluster) ? 2 : plan->npasses;
     for (int i = 0; i < nsched && !plan->uneven && !plan->mixed && !plan->nd; ++i) {
         const PassPlan &pp = plan->pass[i];
         HostSched h = host_sched(pp.logl, pp.loge);
@@ -284,7 +284,7 @@ fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k) {
     if (plan->mixed) {
         mm = mixed_plan_split(plan);
         kk = plan->n / mm;
-    } else if (plan->npasses == 2 || plan->fs) {
+    } else if (plan->npasses == 2 || plan->fs || plan->cluster) {
         mm = int64_t(1) << plan->pass[0].logl;
         kk = plan->n / mm;
     }

@@ -11,6 +11,8 @@ enum PassKind : int {
     KIND_ROWS = 0,   // whole transforms, contiguous lines in and out (single HBM pass)
     KIND_COLS = 1,   // four-step pass 1: column FFTs at stride K, times w_N^(b t'), in place
     KIND_ROWST = 2,  // four-step pass 2: row FFTs, written transposed (stride M)
+    KIND_CLUSTER_A = 3,  // cluster single pass, phase A: column FFTs as KIND_COLS, times
+                         // w_N^(b t'), stored into the peer CTAs' shared memory
 };
 
 enum LayoutId : int { LAYOUT_IL = 0, LAYOUT_SPLIT = 1 };
@@ -56,9 +58,8 @@ struct PassParams {
     // hook that makes every wait run out (the kernels then issue no copy at all)
     int64_t spin_limit;
     int32_t test_no_copy;
-    // tensor-core passes: the fftc_precision of their radix-16 stages (FP16 or BF16, plain
-    // or hi + lo split); 0 for the CUDA-core passes
-    int32_t tc_mode;
+    // KIND_CLUSTER_A: log2 of the rows each CTA of the cluster owns in phase B
+    int32_t cl_log_rows;
 };
 
 typedef cudaError_t (*LaunchFn)(const PassParams &, cudaStream_t);
@@ -70,10 +71,23 @@ struct KernelEntry {
     int smem_bytes;
     LaunchFn launch;
     PrepareFn prepare;
-    int prec;  // fftc_precision of the radix stages (0 = FP32 on CUDA cores)
+    int prec;  // fftc_precision of the radix stages: 0 = FP32 on CUDA cores, 1..4 = the tensor-core mode
     int logx;  // four-step passes: log2 of the compile-time element stride (0 = runtime)
     int pipe;  // > 0: persistent kernel fed by bulk copies through `pipe` landing buffers
 };
+
+// A compiled cluster single pass (fftc_cluster.cuh): n = 2^logn = n1 n2 with n1 = 2^log1,
+// R CTAs per transform, 2^loge elements per thread, one layout in and out. Phase A takes
+// the parameters of a four-step pass 1 (KIND_CLUSTER_A), phase B those of a pass 2.
+typedef cudaError_t (*ClusterLaunchFn)(const PassParams &a, const PassParams &b, int64_t batch, cudaStream_t st);
+struct ClusterEntry {
+    int logn, log1, loge, r, lay;
+    int threads, smem;
+    ClusterLaunchFn launch;
+    PrepareFn prepare;
+};
+int cluster_kernel_count();
+const ClusterEntry *cluster_kernel_at(int i);
 
 // Registry of compiled pass kernels (one table per instantiation unit).
 const KernelEntry *find_kernel(int kind, int logl, int loge, int lines, int lin, int lout, int prec = 0,

@@ -55,8 +55,12 @@ __device__ __forceinline__ unsigned char *dyn_smem_base128() {
     return dyn_raw + ((128 - (smem_u32(dyn_raw) & 127)) & 127);
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0, bool TC = false>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0, int TCM = 0>
 struct Pass {
+    // TCM: 0 = every stage on the CUDA cores; 1..4 = the radix-16 stages on the tensor cores
+    // in that precision mode (TcMode)
+    static constexpr bool TC = TCM != 0;
+    static constexpr int TCM_ID = TCM;
     using Sc = Sched<LOGL, LOGE>;
     static constexpr int L = Sc::L, E = Sc::E, TPL = Sc::TPL, S = Sc::S;
     static constexpr int NT = C * TPL;
@@ -81,7 +85,8 @@ struct Pass {
         for (int i = 0; i < NTC; ++i) f *= 4.f;
         return f;
     }
-    static constexpr bool IN_TAU = (KIND != KIND_COLS);
+    static constexpr bool COLS_LIKE = (KIND == KIND_COLS || KIND == KIND_CLUSTER_A);
+    static constexpr bool IN_TAU = !COLS_LIKE;
     static constexpr bool OUT_TAU = (KIND == KIND_ROWS);
     static constexpr bool MID_TAU = (C < 16);
     static_assert(S > 1 || IN_TAU == OUT_TAU, "a single-stage pass cannot change its mapping");
@@ -101,7 +106,7 @@ struct Pass {
     static constexpr int REG_TARGET = E >= 32 ? 128 : (E >= 16 ? (NT >= 512 ? 64 : 80) : 64);
     static constexpr int MINB = (65536 / (NT * REG_TARGET)) > 0 ? (65536 / (NT * REG_TARGET)) : 1;
     // element strides: compile-time unless LOGX == 0 for a four-step kind
-    static constexpr int ES_IN_CT = (KIND == KIND_COLS) ? (LOGX ? (1 << LOGX) : 0) : 1;
+    static constexpr int ES_IN_CT = COLS_LIKE ? (LOGX ? (1 << LOGX) : 0) : 1;
     static constexpr int ES_OUT_CT = (KIND == KIND_ROWS) ? 1 : (LOGX ? (1 << LOGX) : 0);
     // the four-step workspace is written in the same launch in persistent mode: read it
     // from L2 only, never through a possibly stale L1 line
@@ -162,7 +167,7 @@ struct Pass {
         const int cj = conj_of(p, g, p.conj_out);
         const int es = ES_OUT_CT ? ES_OUT_CT : (int)p.out_elem;
         const float2 *dtab = nullptr;
-        if constexpr (KIND == KIND_COLS) dtab = p.tw2_full ? p.tw2_full + l * (int)p.out_line : nullptr;
+        if constexpr (COLS_LIKE) dtab = p.tw2_full ? p.tw2_full + l * (int)p.out_line : nullptr;
 #pragma unroll
         for (int q = 0; q < E / R; ++q) {
             const int a0 = tau + q * TPL;
@@ -173,7 +178,7 @@ struct Pass {
             for (int t = 0; t < R; ++t) {
                 const int off = t * (L / R) * es;
                 float2 x = v[q * R + t];
-                if constexpr (KIND == KIND_COLS) {
+                if constexpr (COLS_LIKE) {
                     // inter-pass twiddle of Eq. 1 applied at the memory level: w_N^(b t')
                     if (dtab) {
                         x = cmul(x, __ldg(dtab + a0 * es + off));
@@ -184,8 +189,8 @@ struct Pass {
                                          __ldg(p.tw2_hi + (m >> p.tw2_lo_bits))));
                     }
                 }
-                if constexpr (TC) {
-                    if (!tc_is_bf16(p.tc_mode)) {  // FP16 stages ran on data scaled by 1/4 each
+                if constexpr (TC && !tc_is_bf16(TCM)) {
+                    {  // FP16 stages ran on data scaled by 1/4 each
                         x.x *= tc_out_scale();
                         x.y *= tc_out_scale();
                     }
@@ -197,7 +202,14 @@ struct Pass {
                     x.y *= h;
                 }
                 if (cj) x.y = -x.y;
-                if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
+                if constexpr (KIND == KIND_CLUSTER_A) {
+                    // output a of column l goes to row a mod Qb of the CTA that owns rows
+                    // [a - a mod Qb, + Qb) in phase B, position l of that row (row-major)
+                    const int a = a0 + t * (L / R);
+                    const uint32_t rank = (uint32_t)(a >> p.cl_log_rows);
+                    const uint32_t word = (uint32_t)(((a & ((1 << p.cl_log_rows) - 1)) << p.log_lpt) + l);
+                    st_cluster_v2(mapa_shared(smem_u32(dyn_smem_base128()) + 8u * word, rank), x.x, x.y);
+                } else if constexpr (KIND == KIND_COLS && LOUT == LAYOUT_IL) {
                     __stcg(p2 + off, x);  // workspace: keep it in L2 for pass 2
                 } else if constexpr (LOUT == LAYOUT_IL) {
                     __stcs(p2 + off, x);
@@ -291,7 +303,7 @@ struct Pass {
             if constexpr (s > 0 || LANDED) __syncthreads();  // every read of the buffer the A rows alias is done
             // the i-th tensor-core stage of this CTA's k-th tile uses mbarrier phase (k NTC + i) mod 2
             const uint32_t phase = (tk * NTC + tc_count(s)) & 1u;
-            TcUnit<NT>::dft16(p, v, dyn_smem_base128(), smem_u32(sm), phase);
+            TcUnit<NT, TCM>::dft16(p, v, dyn_smem_base128(), smem_u32(sm), phase);
             __syncthreads();  // every group's MMA has read its A rows
             if constexpr (H::active && s == S - 1) hook();  // the tile buffer is free
         } else {
@@ -352,7 +364,7 @@ struct Pass {
             // persistent: the set-up (DFT matrices, mbarriers, TMEM columns) is paid once per CTA
             unsigned char *area = dyn_smem_base128();
             float2 *sm = reinterpret_cast<float2 *>(area + TC_BYTES);
-            TcUnit<NT>::setup(p, area);
+            TcUnit<NT, TCM>::setup(p, area);
             const int64_t ntiles = (p.total_lines + C - 1) / C;
             uint32_t tk = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tk) {
@@ -361,7 +373,7 @@ struct Pass {
                 stage<0>(p, sm, v, threadIdx.x, tile * C, NoHook(), tk);
                 __syncthreads();  // the tile's last shared reads precede the next tile's A rows
             }
-            TcUnit<NT>::teardown(area);
+            TcUnit<NT, TCM>::teardown(area);
         } else {
             stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
         }
@@ -383,11 +395,11 @@ struct Pass {
     }
 };
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
-__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>::NT,
-                                  Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>::MINB)
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int TCM = 0>
+__global__ void __launch_bounds__(Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>::NT,
+                                  Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>::MINB)
     k_pass(const __grid_constant__ PassParams p) {
-    Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>::run(p);
+    Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>::run(p);
 }
 
 // CTAs of a kernel that fit on one SM at once. For kernels that allocate tensor memory
@@ -420,58 +432,58 @@ inline int resident_per_sm(const void *func, int threads, int dyn_smem, int tmem
 }
 
 // CTAs of a k_pass instance resident on the current device at once (0 if unknown)
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int TCM = 0>
 int resident_ctas() {
     static int r = -1;
     if (r < 0) {
-        using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
+        using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>;
         int sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;
-        const int per_sm = resident_per_sm((const void *)k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>, P::NT,
-                                           P::SMEM, TC ? (int)tc_tmem_cols(P::NT) : 0);
+        const int per_sm = resident_per_sm((const void *)k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>, P::NT,
+                                           P::SMEM, TCM ? (int)tc_tmem_cols(P::NT) : 0);
         r = per_sm * sms;
     }
     return r;
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int TCM = 0>
 cudaError_t launch_pass(const PassParams &p, cudaStream_t st) {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>;
     const int64_t blocks = (p.total_lines + C - 1) / C;
     if (blocks <= 0) return cudaSuccess;
-    if constexpr (TC) {  // persistent: one wave of CTAs walks the tiles
-        const int res = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>();
+    if constexpr (TCM != 0) {  // persistent: one wave of CTAs walks the tiles
+        const int res = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>();
         if (res <= 0) return cudaErrorInvalidConfiguration;
         const unsigned grid = (unsigned)(blocks < res ? blocks : res);
-        k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC><<<grid, P::NT, P::SMEM, st>>>(p);
+        k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM><<<grid, P::NT, P::SMEM, st>>>(p);
         return cudaGetLastError();
     }
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     if constexpr (KIND == KIND_COLS) {
         if (p.pf_tiles < 0) {
             PassParams q = p;
-            q.pf_tiles = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>();
-            k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(q);
+            q.pf_tiles = resident_ctas<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>();
+            k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(q);
             return cudaGetLastError();
         }
     }
-    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
+    k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM><<<(unsigned)blocks, P::NT, P::SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, bool TC = false>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int TCM = 0>
 cudaError_t prepare_pass() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>;
     if (P::SMEM <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>,
+    return cudaFuncSetAttribute(k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
 }
 
-template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX = 0, bool TC = false>
+template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX = 0, int TCM = 0>
 constexpr KernelEntry entry() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>;
     return KernelEntry{KIND,
                        LOGL,
                        LOGE,
@@ -480,9 +492,9 @@ constexpr KernelEntry entry() {
                        LOUT,
                        P::NT,
                        P::SMEM,
-                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>,
-                       &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TC>,
-                       TC ? 1 : 0,
+                       &launch_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>,
+                       &prepare_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>,
+                       TCM,
                        LOGX,
                        0};
 }

@@ -51,7 +51,7 @@ struct PipeTile {
         const PassParams &p = a.p;
         if (p.test_no_copy) return;  // test hook: the barrier is never armed, its wait runs out
         const int64_t g0 = tile * C;
-        if constexpr (KIND == KIND_COLS) {
+        if constexpr (P::COLS_LIKE) {
             const int tr = (int)(g0 >> p.log_lpt), b0 = (int)(g0 & ((int64_t(1) << p.log_lpt) - 1));
             mbar_arrive_expect_tx(bar, (uint32_t)(L * C * sizeof(float2)));
 #pragma unroll
@@ -121,7 +121,7 @@ struct PipeTile {
             for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
             fence_mbar_init();
         }
-        if constexpr (P::NTC > 0) TcUnit<NT>::setup(p, area);  // ends with a CTA barrier
+        if constexpr (P::NTC > 0) TcUnit<NT, P::TCM_ID>::setup(p, area);  // ends with a CTA barrier
         __syncthreads();
         if (threadIdx.x == 0)
             for (int b = 0; b < NBUF; ++b) {
@@ -154,7 +154,7 @@ struct PipeTile {
                 if (next < ntiles) refill(a, next, buf, &bars[b]);
             }
         }
-        if constexpr (P::NTC > 0) TcUnit<NT>::teardown(area);
+        if constexpr (P::NTC > 0) TcUnit<NT, P::TCM_ID>::teardown(area);
     }
 };
 
@@ -209,12 +209,12 @@ constexpr int pipe_code(int nbuf, bool early) { return nbuf | (early ? 4 : 0); }
 
 // registry entry of a pipelined pass kernel
 template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, int LOGX, int NBUF, bool EARLY = false,
-          bool TC = false>
+          int TCM = 0>
 constexpr KernelEntry pipe_entry() {
-    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TC>;
+    using P = Pass<LOGL, LOGE, C, KIND, LIN, LOUT, false, LOGX, TCM>;
     using L = PipeLauncher<P, NBUF, EARLY>;
     return KernelEntry{KIND,          LOGL, LOGE, C, LIN, LOUT, P::NT, PipeTile<P, NBUF, EARLY>::SMEM,
-                       &L::launch,    &L::prepare, TC ? 1 : 0, LOGX, pipe_code(NBUF, EARLY)};
+                       &L::launch,    &L::prepare, TCM, LOGX, pipe_code(NBUF, EARLY)};
 }
 
 }  // namespace fftc

@@ -154,7 +154,6 @@ void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams 
     const int64_t n = p->n, B = p->batch, M = int64_t(1) << logm, K = n >> logm;
     const int logk = p->logn - logm;
     const int64_t plane = p->layout == FFTC_LAYOUT_SPLIT ? n * B : 0;
-    const int tcm = p->precision != FFTC_FP32 ? (int)p->precision : 0;
     memset(&a, 0, sizeof(a));
     a.err = p->d_err;
     set_wait_hooks(a);
@@ -173,7 +172,6 @@ void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams 
     a.tw2_full = p->tw2_full;
     a.log_n2 = p->logn;
     a.tw2_lo_bits = p->tw2_lo_bits;
-    a.tc_mode = tcm;
     memset(&b, 0, sizeof(b));
     b.err = p->d_err;
     set_wait_hooks(b);
@@ -189,12 +187,68 @@ void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams 
     b.out_elem = M;
     b.post_line_mul = 1;
     b.post_elem_mul = M;
-    b.tc_mode = tcm;
+}
+
+// Default cluster single pass per size (measured): clusters of R CTAs of Q = n / R points.
+struct ClusterDefault {
+    int logn, log1, r;
+};
+static const ClusterDefault kClusterDefaults[] = {{15, 7, 4}, {16, 8, 8}, {17, 8, 16}, {18, 9, 16}};
+
+const ClusterEntry *cluster_default(int logn, int lay) {
+    int log1 = 0, r = 0;
+    for (const ClusterDefault &d : kClusterDefaults)
+        if (d.logn == logn) {
+            log1 = d.log1;
+            r = d.r;
+        }
+    r = env_int("FFTC_TUNE_CLUSTER_R", r);
+    const ClusterEntry *any = nullptr;
+    for (int i = 0; i < cluster_kernel_count(); ++i) {
+        const ClusterEntry *e = cluster_kernel_at(i);
+        if (e->logn != logn || e->lay != lay) continue;
+        if (e->r == r && (e->log1 == log1 || !any)) return e;
+        if (!any) any = e;
+    }
+    return any;
+}
+
+fftc_status cluster_setup(fftc_plan_s *p, const ClusterEntry *ce) {
+    if (p->tw2_full) plan_release(p, p->tw2_full);
+    p->tw2_full = nullptr;
+    fftc_status s = upload_full_diagonal(p, ce->log1, &p->tw2_full);
+    if (s != FFTC_OK) return s;
+    const int log2 = p->logn - ce->log1;
+    int logr = 0;
+    while ((1 << logr) < ce->r) ++logr;
+    PassPlan &pa = p->pass[0], &pb = p->pass[1];
+    four_step_params(p, ce->log1, pa.base, pb.base);
+    pa.base.cl_log_rows = ce->log1 - logr;  // rows of phase B per CTA: n1 / R
+    pa.kind = KIND_CLUSTER_A;
+    pa.logl = ce->log1;
+    pa.loge = ce->loge;
+    pa.lines = (1 << log2) / ce->r;
+    pa.lin = ce->lay;
+    pa.lout = LAYOUT_IL;
+    pa.k = nullptr;
+    pb.kind = KIND_ROWST;
+    pb.logl = log2;
+    pb.loge = ce->loge;
+    pb.lines = (1 << ce->log1) / ce->r;
+    pb.lin = LAYOUT_IL;
+    pb.lout = ce->lay;
+    pb.k = nullptr;
+    if ((s = upload_stage_tables(p, pa)) != FFTC_OK) return s;
+    if ((s = upload_stage_tables(p, pb)) != FFTC_OK) return s;
+    if (ce->prepare() != cudaSuccess) return FFTC_ERR_CUDA;
+    p->cluster = ce;
+    p->npasses = 1;
+    return FFTC_OK;
 }
 
 fftc_status plan_build_passes(fftc_plan_s *p) {
     const bool tc = p->precision != FFTC_FP32;
-    const int prec = tc ? 1 : 0;  // registry tag of the tensor-core kernels (the mode is a run-time argument)
+    const int prec = tc ? (int)p->precision : 0;  // registry tag: the tensor-core precision mode
     if (tc && (p->logn < 7 || p->logn > 16)) return FFTC_ERR_UNSUPPORTED_SIZE;
     const int64_t n = p->n, B = p->batch;
     const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
@@ -245,7 +299,6 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         memset(&b, 0, sizeof(b));
         b.err = p->d_err;
         set_wait_hooks(b);
-        b.tc_mode = tc ? (int)p->precision : 0;
         b.in_plane = b.out_plane = plane;
         b.total_lines = B;
         b.log_lpt = 0;
@@ -257,6 +310,12 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         fftc_status s = upload_stage_tables(p, pp);
         if (s != FFTC_OK) return s;
         return prepare(pp);
+    }
+
+    // one HBM round trip on a thread-block cluster (FP32, n = 2^15 .. 2^18)
+    if (!tc && env_int("FFTC_CLUSTER", 0)) {
+        const ClusterEntry *ce = cluster_default(p->logn, lay);
+        if (ce) return cluster_setup(p, ce);
     }
 
     // four-step: n = M * K
@@ -384,6 +443,18 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
         return s;
     }
     if (ev) cudaEventRecord(ev[0], st);
+    if (p->cluster) {
+        PassParams a = p->pass[0].base, b = p->pass[1].base;
+        a.in = (const float *)in;
+        a.conj_in = inv;
+        b.out = (float *)out;
+        b.conj_out = inv;
+        b.post_h = post_h;
+        b.post_scale = post_scale;
+        if (p->cluster->launch(a, b, p->batch, st) != cudaSuccess) return FFTC_ERR_CUDA;
+        if (ev) cudaEventRecord(ev[1], st);
+        return FFTC_OK;
+    }
     if (p->fs) {
         fftc_status s = fs_run(p, in, out, post_h, post_scale, st);
         if (ev) cudaEventRecord(ev[1], st);
@@ -434,6 +505,13 @@ fftc_status plan_run_range(fftc_plan_s *p, const void *in, void *out, int64_t b0
     a.total_lines = a.total_lines / p->batch * nb;
     a.in = src;
     a.conj_in = inv;
+    if (p->cluster) {
+        PassParams b = p->pass[1].base;
+        b.total_lines = b.total_lines / p->batch * nb;
+        b.out = dst;
+        b.conj_out = inv;
+        return p->cluster->launch(a, b, nb, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+    }
     if (p->npasses == 1) {
         a.out = dst;
         a.conj_out = inv;

@@ -50,6 +50,9 @@ struct fftc_plan_s {
     fftc::MixedState *mixed = nullptr;  // n with factors 3, 5 or 7 (fftc_mixed.cu)
     fftc::NdState *nd = nullptr;        // rank 2 / 3 transforms (fftc_mixed.cu)
     int64_t force_m = 0;  // mixed radix: the split n = M K chosen by measure-mode planning (0: default)
+    // cluster single pass (one HBM round trip for n = 2^15 .. 2^18): pass[0] holds phase A
+    // (columns of n1), pass[1] phase B (rows of n2); npasses = 1
+    const fftc::ClusterEntry *cluster = nullptr;
     std::vector<void *> dev_allocs;
     // timing probe: events[slot * 3 + i] before pass i (i < npasses) and after the last
     std::vector<cudaEvent_t> probe_events;
@@ -68,6 +71,10 @@ fftc_status plan_build(fftc_plan_s *p);
 // and both passes' parameters from the plan's tables (kernels and stage tables aside)
 fftc_status upload_full_diagonal(fftc_plan_s *p, int logm, float2 **out);
 void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams &b);
+// cluster single pass: switch the plan to `ce` (tables, parameters); the default entry of
+// the plan's n and layout, or NULL where none is compiled
+fftc_status cluster_setup(fftc_plan_s *p, const ClusterEntry *ce);
+const ClusterEntry *cluster_default(int logn, int lay);
 // release one device allocation made through plan_alloc / plan_upload
 void plan_release(fftc_plan_s *p, void *ptr);
 // Enqueue the plan on `st`. post_h (device, n floats, may be NULL) multiplies every

@@ -95,6 +95,32 @@ __device__ __forceinline__ bool mbar_wait_sleepy(uint64_t *bar, uint32_t parity,
 
 
 // ---------------------------------------------------------------------------
+// thread-block clusters: distributed shared memory and the cluster barrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// the address in the shared memory of CTA `rank` of the cluster of a local shared address
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, float x, float y) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(x), "f"(y) : "memory");
+}
+
+// every thread of every CTA of the cluster: writes before it (local and distributed shared
+// memory) are visible to every thread of the cluster after it
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // tcgen05: fifth-generation tensor cores with accumulators in tensor memory (TMEM)
 // ---------------------------------------------------------------------------
 

@@ -3,10 +3,11 @@
 
 namespace fftc {
 
-extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcRowsTable[],
-    kTc4Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[],
+extern const KernelEntry kRowsIlTable[], kRowsSplitTable[], kColsTable[], kRowsTTable[], kTcRowsM1Table[],
+    kTcRowsM2Table[], kTcRowsM3Table[], kTcRowsM4Table[], kTc4M1Table[], kTc4M2Table[], kTc4M3Table[], kTc4M4Table[], kPipeRowsIlTable[], kPipeRowsSplitTable[], kPipe4Table[], kPipeEarlyIlTable[], kPipeEarlySplitTable[],
     kColsSplitTable[], kLargeTable[], kPipeLargeTable[];
-extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcRowsCount, kTc4Count,
+extern const int kRowsIlCount, kRowsSplitCount, kColsCount, kRowsTCount, kTcRowsM1Count, kTcRowsM2Count, kTcRowsM3Count,
+    kTcRowsM4Count, kTc4M1Count, kTc4M2Count, kTc4M3Count, kTc4M4Count,
     kPipeRowsIlCount, kPipeRowsSplitCount, kPipe4Count, kPipeEarlyIlCount, kPipeEarlySplitCount, kColsSplitCount, kLargeCount, kPipeLargeCount;
 
 struct TableRef {
@@ -16,7 +17,9 @@ struct TableRef {
 static const TableRef kTables[] = {
     {kRowsIlTable, &kRowsIlCount}, {kRowsSplitTable, &kRowsSplitCount},
     {kColsTable, &kColsCount}, {kRowsTTable, &kRowsTCount},
-    {kTcRowsTable, &kTcRowsCount}, {kTc4Table, &kTc4Count},
+    {kTcRowsM1Table, &kTcRowsM1Count}, {kTcRowsM2Table, &kTcRowsM2Count},
+    {kTcRowsM3Table, &kTcRowsM3Count}, {kTcRowsM4Table, &kTcRowsM4Count}, {kTc4M1Table, &kTc4M1Count},
+    {kTc4M2Table, &kTc4M2Count}, {kTc4M3Table, &kTc4M3Count}, {kTc4M4Table, &kTc4M4Count},
     {kPipeRowsIlTable, &kPipeRowsIlCount}, {kPipeRowsSplitTable, &kPipeRowsSplitCount}, {kPipe4Table, &kPipe4Count},
     {kPipeEarlyIlTable, &kPipeEarlyIlCount}, {kPipeEarlySplitTable, &kPipeEarlySplitCount},
     {kColsSplitTable, &kColsSplitCount}, {kLargeTable, &kLargeCount},

@@ -35,7 +35,7 @@
 
 namespace fftc {
 
-// tc_mode of PassParams (the fftc_precision values)
+// precision modes of the tensor-core passes (the fftc_precision values)
 enum TcMode : int { TC_FP16 = 1, TC_BF16 = 2, TC_FP16_SPLIT = 3, TC_BF16_SPLIT = 4 };
 
 __host__ __device__ constexpr bool tc_is_bf16(int mode) { return mode == TC_BF16 || mode == TC_BF16_SPLIT; }
@@ -112,15 +112,18 @@ __host__ __device__ constexpr uint32_t tc_tmem_cols(int nt) {
     return nt <= 128 ? 32u : (nt <= 256 ? 64u : (nt <= 512 ? 128u : 256u));
 }
 
-template <int NT>
+template <int NT, int MODE>
 struct TcUnit {
     static_assert(NT % 128 == 0 && NT <= 1024, "whole 128-thread MMA groups");
+    static_assert(MODE >= TC_FP16 && MODE <= TC_BF16_SPLIT, "a tensor-core precision mode");
+    static constexpr bool BF = tc_is_bf16(MODE), SPLIT = tc_is_split(MODE);
     static constexpr int NWG = NT / 128;
     static constexpr uint32_t COLS = tc_tmem_cols(NT);
 
     // every thread: DFT matrices into shared memory, mbarriers, TMEM columns
     __device__ static void setup(const PassParams &p, unsigned char *area) {
-        const bool bf = tc_is_bf16(p.tc_mode);
+        (void)p;
+        constexpr bool bf = BF;
         for (int i = threadIdx.x; i < 32 * 32; i += NT) {
             const int n = i >> 5, k = i & 31;
             const float v = tc_b_value(n, k);
@@ -154,10 +157,9 @@ struct TcUnit {
     // (every read of the aliased buffer done) and after (every group's MMA done).
     __device__ __forceinline__ static void dft16(const PassParams &p, float2 (&v)[16], unsigned char *area,
                                                  uint32_t a_smem, uint32_t phase) {
-        const int mode = p.tc_mode;
-        const bool bf = tc_is_bf16(mode), split = tc_is_split(mode);
+        constexpr bool bf = BF, split = SPLIT;
         const int tid = threadIdx.x, wg = tid >> 7, m = tid & 127;
-        if (!bf) {
+        if constexpr (!bf) {
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 v[t].x *= 0.25f;
@@ -166,7 +168,7 @@ struct TcUnit {
         }
         const uint32_t aw = a_smem + wg * kTcAGroupBytes;
         const uint32_t row = aw + (m >> 3) * kTcASbo + (m & 7) * 16;
-        if (split) {
+        if constexpr (split) {
             uint32_t hr[8], hi_[8], lr[8], li[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -205,7 +207,7 @@ struct TcUnit {
             // K = 16 steps: (A chunks, B chunks) = (re, re-rows of B), (im, im-rows of B)
             umma_f16(d, umma_desc(aw, 128, kTcASbo), umma_desc(bhi, 128, 512), idesc, 0);
             umma_f16(d, umma_desc(aw + 256, 128, kTcASbo), umma_desc(bhi + 256, 128, 512), idesc, 1);
-            if (split) {
+            if constexpr (split) {
                 umma_f16(d, umma_desc(aw + 512, 128, kTcASbo), umma_desc(bhi, 128, 512), idesc, 1);        // lo.hi
                 umma_f16(d, umma_desc(aw + 768, 128, kTcASbo), umma_desc(bhi + 256, 128, 512), idesc, 1);
                 umma_f16(d, umma_desc(aw, 128, kTcASbo), umma_desc(blo, 128, 512), idesc, 1);              // hi.lo

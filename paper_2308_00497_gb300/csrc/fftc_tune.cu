@@ -10,7 +10,8 @@
 //                (plain with and without the L2 prefetch, tensor-map fed; compile-time
 //                or runtime stride; each radix schedule) and every transposed-row kernel
 //                for pass 2, timed pass by pass; the split with the smallest sum wins.
-// Choices are cached per (n, batch, layout, direction) for the process.
+// Tensor-core plans choose among the tensor-core kernels of their precision mode.
+// Choices are cached per (n, batch, layout, direction, precision) for the process.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -28,13 +29,16 @@ struct Choice {
     int logm = 0;  // four-step split n = 2^logm * 2^(logn - logm) (unused for one pass)
     const KernelEntry *k1 = nullptr, *k2 = nullptr;
     int pf1 = 0;
+    const ClusterEntry *cl = nullptr;  // the cluster single pass instead of the above
 };
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int64_t, int, int>, Choice> g_tune_cache;
+std::map<std::tuple<int64_t, int64_t, int, int, int>, Choice> g_tune_cache;
 
 struct Scratch {
     void *in = nullptr, *out = nullptr;
+    void *ws = nullptr;  // the four-step workspace: the plan's, or a scratch one when it has none
+    bool own_ws = false;
     cudaStream_t st = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     ~Scratch() {
@@ -43,6 +47,7 @@ struct Scratch {
         if (st) cudaStreamDestroy(st);
         if (in) cudaFree(in);
         if (out) cudaFree(out);
+        if (own_ws && ws) cudaFree(ws);
     }
 };
 
@@ -84,6 +89,31 @@ float time_launch(const KernelEntry *k, const PassParams &a, Scratch &s, int rep
 }
 
 fftc_status apply(fftc_plan_s *p, const Choice &c, std::map<std::pair<int, int>, const float2 *> &tabs) {
+    if (c.cl) {  // one HBM round trip on a cluster: no workspace
+        if (p->cluster != c.cl) {
+            fftc_status st = cluster_setup(p, c.cl);
+            if (st != FFTC_OK) return st;
+        }
+        if (p->workspace) plan_release(p, p->workspace);
+        p->workspace = nullptr;
+        return FFTC_OK;
+    }
+    if (p->cluster) {  // back from the cluster pass to the two four-step passes
+        const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
+        void *d = nullptr;
+        if (plan_alloc(p, (size_t)p->total_elems * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        p->workspace = (float2 *)d;
+        p->cluster = nullptr;
+        p->npasses = 2;
+        PassPlan &q0 = p->pass[0], &q1 = p->pass[1];
+        q0.kind = KIND_COLS;
+        q0.lin = lay;
+        q0.lout = LAYOUT_IL;
+        q0.logl = -1;  // forces the split's tables and parameters below
+        q1.kind = KIND_ROWST;
+        q1.lin = LAYOUT_IL;
+        q1.lout = lay;
+    }
     const float2 *t0 = nullptr, *t1 = nullptr;
     if (!tables_for(p, tabs, c.k1->logl, c.k1->loge, &t0)) return FFTC_ERR_ALLOC;
     if (p->npasses == 2 && !tables_for(p, tabs, c.k2->logl, c.k2->loge, &t1)) return FFTC_ERR_ALLOC;
@@ -118,6 +148,47 @@ fftc_status apply(fftc_plan_s *p, const Choice &c, std::map<std::pair<int, int>,
     return FFTC_OK;
 }
 
+// registry tag of the plan's kernels: 0 (FP32 on CUDA cores) or the tensor-core mode
+int prec_of(const fftc_plan_s *p) { return p->precision == FFTC_FP32 ? 0 : (int)p->precision; }
+
+// time of the cluster single pass `ce` on the plan's shape (its own diagonal and tables)
+float time_cluster(fftc_plan_s *p, const ClusterEntry *ce, Scratch &s, int reps,
+                   std::map<std::pair<int, int>, const float2 *> &tabs, fftc_status *err) {
+    if (ce->prepare() != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    float2 *diag = nullptr;
+    if ((*err = upload_full_diagonal(p, ce->log1, &diag)) != FFTC_OK) return -1.f;
+    const int log2 = p->logn - ce->log1, inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    int logr = 0;
+    while ((1 << logr) < ce->r) ++logr;
+    PassParams a, b;
+    four_step_params(p, ce->log1, a, b);
+    a.tw2_full = diag;
+    a.cl_log_rows = ce->log1 - logr;
+    a.in = (const float *)s.in;
+    a.conj_in = inv;
+    b.out = (float *)s.out;
+    b.conj_out = inv;
+    float ms = -1.f;
+    if (!tables_for(p, tabs, ce->log1, ce->loge, &a.tw) || !tables_for(p, tabs, log2, ce->loge, &b.tw)) {
+        *err = FFTC_ERR_ALLOC;
+    } else if (ce->launch(a, b, p->batch, s.st) == cudaSuccess && cudaStreamSynchronize(s.st) == cudaSuccess) {
+        cudaEventRecord(s.a, s.st);
+        for (int i = 0; i < reps; ++i) ce->launch(a, b, p->batch, s.st);
+        cudaEventRecord(s.b, s.st);
+        if (cudaEventSynchronize(s.b) == cudaSuccess) {
+            cudaEventElapsedTime(&ms, s.a, s.b);
+            ms /= reps;
+        }
+    } else {
+        cudaGetLastError();
+    }
+    plan_release(p, diag);
+    return ms;
+}
+
 // fastest pass-1 and pass-2 kernels of one four-step split, with their summed time
 float time_split(fftc_plan_s *p, int logm, const float2 *diag, Scratch &s, int reps,
                  std::map<std::pair<int, int>, const float2 *> &tabs, Choice *out, fftc_status *err) {
@@ -131,7 +202,7 @@ float time_split(fftc_plan_s *p, int logm, const float2 *diag, Scratch &s, int r
     c.logm = logm;
     for (int i = 0; i < kernel_count(); ++i) {
         const KernelEntry *e = kernel_at(i);
-        if (e->prec != 0) continue;
+        if (e->prec != prec_of(p)) continue;
         if (e->kind == KIND_COLS && e->logl == logm && e->lin == lay && e->lout == LAYOUT_IL &&
             (e->logx == 0 || e->logx == logk)) {
             for (int pf : {0, -1}) {
@@ -143,7 +214,7 @@ float time_split(fftc_plan_s *p, int logm, const float2 *diag, Scratch &s, int r
                 }
                 a.pf_tiles = pf;
                 a.in = (const float *)s.in;
-                a.out = (float *)p->workspace;
+                a.out = (float *)s.ws;
                 a.conj_in = inv;
                 const float t = time_launch(e, a, s, reps);
                 if (t > 0.f && t < t1) {
@@ -159,7 +230,7 @@ float time_split(fftc_plan_s *p, int logm, const float2 *diag, Scratch &s, int r
                 *err = FFTC_ERR_ALLOC;
                 return -1.f;
             }
-            b.in = (const float *)p->workspace;
+            b.in = (const float *)s.ws;
             b.out = (float *)s.out;
             b.conj_out = inv;
             const float t = time_launch(e, b, s, reps);
@@ -180,10 +251,10 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
     if (p->batch == 0) return FFTC_OK;
     if (p->mixed) return mixed_tune(p, reps);
     if (p->nd) return nd_tune(p, reps);
-    if (p->uneven || p->fs || p->precision != FFTC_FP32) return FFTC_OK;
+    if (p->uneven || p->fs) return FFTC_OK;
     if (reps < 1) reps = 1;
     const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
-    const auto key = std::make_tuple(p->n, p->batch, (int)p->layout, (int)p->direction);
+    const auto key = std::make_tuple(p->n, p->batch, (int)p->layout, (int)p->direction, (int)p->precision);
     std::map<std::pair<int, int>, const float2 *> tabs;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -202,12 +273,13 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
     best.k1 = p->pass[0].k;
     best.k2 = p->npasses == 2 ? p->pass[1].k : nullptr;
     best.pf1 = p->pass[0].base.pf_tiles;
+    best.cl = p->cluster;  // the plan as built, unless a candidate is faster
     const PassPlan &p0 = p->pass[0];
-    if (p->npasses == 1) {
+    if (p->npasses == 1 && !p->cluster) {
         float t1 = 1e30f;
         for (int i = 0; i < kernel_count(); ++i) {
             const KernelEntry *e = kernel_at(i);
-            if (e->prec != 0 || e->kind != KIND_ROWS || e->logl != p0.logl || e->lin != lay || e->lout != lay)
+            if (e->prec != prec_of(p) || e->kind != KIND_ROWS || e->logl != p0.logl || e->lin != lay || e->lout != lay)
                 continue;
             PassParams a = p0.base;
             if (!tables_for(p, tabs, e->logl, e->loge, &a.tw)) return FFTC_ERR_ALLOC;
@@ -221,14 +293,20 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
             }
         }
     } else {
+        if (p->workspace) {
+            s.ws = p->workspace;
+        } else {
+            if (cudaMalloc(&s.ws, bytes) != cudaSuccess) return FFTC_ERR_ALLOC;
+            s.own_ws = true;
+        }
         // every split M K whose factors have compiled kernels (columns 2^6..2^12, rows 2^7..2^12)
         float tbest = 1e30f;
         for (int logm = 6; logm <= 12; ++logm) {
             const int logk = p->logn - logm;
             if (logk < 7 || logk > 12) continue;
             float2 *diag = nullptr;
-            if (p->tw2_full) {  // the whole diagonal of this split (n <= 2^20)
-                if (logm == p0.logl) {
+            if (p->logn <= 20) {  // the whole diagonal of this split
+                if (logm == p0.logl && p->tw2_full && !p->cluster) {
                     diag = p->tw2_full;
                 } else {
                     fftc_status st = upload_full_diagonal(p, logm, &diag);
@@ -245,8 +323,21 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
                 best = c;
             }
         }
+        // one HBM round trip on a thread-block cluster, every compiled shape for n and layout
+        for (int i = 0; i < cluster_kernel_count() && p->precision == FFTC_FP32; ++i) {
+            const ClusterEntry *ce = cluster_kernel_at(i);
+            if (ce->logn != p->logn || ce->lay != lay) continue;
+            fftc_status err = FFTC_OK;
+            const float t = time_cluster(p, ce, s, reps, tabs, &err);
+            if (err != FFTC_OK) return err;
+            if (t > 0.f && t < tbest) {
+                tbest = t;
+                best = Choice();
+                best.cl = ce;
+            }
+        }
     }
-    if (!best.k1 || (p->npasses == 2 && !best.k2)) return FFTC_ERR_UNSUPPORTED_SIZE;
+    if (!best.cl && (!best.k1 || ((p->npasses == 2 || p->cluster) && !best.k2))) return FFTC_ERR_UNSUPPORTED_SIZE;
     const fftc_status st = apply(p, best, tabs);
     if (st != FFTC_OK) return st;
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -333,3 +333,59 @@ def test_l2_resident_counter_wait_reports_timeout(monkeypatch, layout):
     """The L2-resident four-step spins on per-group counters; with the hook every awaited
     count is out of reach, so each spin runs out after its poll limit."""
     _timeout_then_recover(monkeypatch, 1 << 16, 8, layout, {"FFTC_L2_RESIDENT": "1"})
+
+
+@pytest.mark.parametrize("e,r", [(15, 4), (15, 2), (16, 8), (16, 4), (17, 16), (17, 8), (18, 16)])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_cluster_single_pass(monkeypatch, e, r, layout, inverse):
+    """The thread-block-cluster single pass (one HBM round trip, the middle permutation of
+    Eq. 1 through distributed shared memory) for every compiled cluster shape, both layouts
+    and directions, every row against the oracle; a batch that is not a multiple of the
+    clusters resident at once."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_CLUSTER", "1")
+    monkeypatch.setenv("FFTC_TUNE_CLUSTER_R", str(r))
+    n = 1 << e
+    B = 5
+    x = si.uniform_complex(B, n, seed=e * 10 + r)
+    p = fc.Plan(n, B, layout, inverse)
+    passes, radices = p.info()
+    m, k = p.split()
+    assert passes == 1 and m * k == n and int(np.prod(radices)) == n
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    ref = oracle.fft(x.astype(np.complex128), inverse=inverse)
+    assert rel_l2_rows(y, ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e", [15, 16, 17, 18])
+def test_cluster_full_size_and_pointwise(monkeypatch, e):
+    """Sweep shape (n * batch = 2^26: many transforms per cluster) on sampled rows, in place,
+    and the fused per-frequency factor of the spectral filter through the cluster pass."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_CLUSTER", "1")
+    n = 1 << e
+    B = (1 << 26) // n
+    x = si.uniform_complex(B, n, seed=300 + e)
+    rows = np.array([0, 1, B // 2, B - 1])
+    p = fc.Plan(n, B)
+    t = to_device(x, "interleaved")
+    p.execute(t, t)
+    torch.cuda.synchronize()
+    p.check()
+    ref = oracle.fft(x[rows].astype(np.complex128))
+    assert rel_l2_rows(t[torch.from_numpy(rows).cuda()].cpu().numpy(), ref).max() <= tol_fp32(n)
+    h = torch.from_numpy(si.gaussian_lowpass(n)).cuda()
+    xs = to_device(x[:4], "interleaved")
+    q = fc.Plan(n, 4)
+    y = q.execute_pointwise(xs, h, 0.5).cpu().numpy()
+    want = oracle.fft(x[:4].astype(np.complex128)) * (0.5 * si.gaussian_lowpass(n))[None, :]
+    assert rel_l2_rows(y, want).max() <= tol_fp32(n)
+
+
+def test_cluster_landing_wait_reports_timeout(monkeypatch):
+    """The cluster pass's landing waits run out with the hook: every CTA sets the error word
+    and still runs its cluster barriers, so the launch ends and the status is reported."""
+    _timeout_then_recover(monkeypatch, 1 << 16, 9, "split", {"FFTC_CLUSTER": "1"})

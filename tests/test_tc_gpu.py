@@ -130,3 +130,23 @@ def test_precision_workload_full_batch_sampled(e):
         y = _run(x, "interleaved", False, mode)
         err = rel_l2_rows(y[rows], ref).max()
         assert err <= bound(mode, n), (mode, n, float(err))
+
+
+@pytest.mark.parametrize("mode", ["fp16_tc_split", "bf16_tc"])
+@pytest.mark.parametrize("e", [10, 12, 15])
+def test_tuned_tc_plan(mode, e):
+    """Measure-mode planning of a tensor-core plan picks among that mode's kernels only and
+    stays within the mode's bound; replays are bit-identical."""
+    import paper_2308_00497_gb300 as fc
+    n = 1 << e
+    B = max(4, (1 << 20) // n)
+    x = si.gaussian_complex(B, n, seed=700 + e)
+    p = fc.Plan(n, B, "interleaved", False, mode).tune(2)
+    xd = to_device(x, "interleaved")
+    a = p.execute(xd)
+    b = p.execute(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    rows = np.array([0, B - 1])
+    ref = oracle.fft(x[rows].astype(np.complex128))
+    assert rel_l2_rows(from_device(a, "interleaved")[rows], ref).max() <= bound(mode, n)
