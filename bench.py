@@ -249,7 +249,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
         B = ELEMS // n
         for layout in args.layouts:
             for inv in args.dirs:
-                pl = fc.Plan(n, B, layout, inv, device=dev)
+                pl = fc.Plan(n, B, layout, inv, precision=args.precision, device=dev)
                 if args.tune:
                     pl.tune(3)  # measure-mode planning, outside the timed region
                 plans.append((e, layout, inv, pl))
@@ -308,6 +308,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
             k["launches"] += cnt
         t_exec = sum(pm[:passes]) / max(cnt, 1)
         per_size.append({"n": n, "layout": layout, "dir": "inv" if inv else "fwd", "passes": passes,
+                         "split": list(p.split()),
                          "ms": round(t_exec, 4), "gflops": round(flops(n, ELEMS // n) / t_exec / 1e6, 1),
                          "hbm_frac_strict": round(16.0 * ELEMS / (t_exec * 1e-3) / 1e9 / peaks()[0], 4),
                          "hbm_frac_per_pass": round(16.0 * ELEMS * passes / (t_exec * 1e-3) / 1e9 / peaks()[0], 4)})
@@ -364,7 +365,8 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": "2^8..2^20", "n_times_batch": ELEMS,
                        "layouts": LAYOUTS, "directions": ["forward", "inverse"],
                        "l2": "no flush: every buffer is 512 MiB, larger than L2",
@@ -641,6 +643,8 @@ def main():
     ap.add_argument("--sizes", default=",".join(str(e) for e in SIZES),
                     help="log2 n list (default: the whole sweep); a subset is for profiling only")
     ap.add_argument("--layouts", default=",".join(LAYOUTS))
+    ap.add_argument("--precision", default="fp32",
+                    help="precision of the sweep plans (fp32; the tensor-core modes for n = 2^7..2^16): for profiling")
     ap.add_argument("--dirs", default="fwd,inv")
     ap.add_argument("--tune", type=int, default=1,
                     help="1: measure-mode planning (fftc_plan_tune) before timing; 0: the default table")

@@ -82,13 +82,40 @@ struct WorkItem {
 struct PersArgs {
     const WorkItem *items;
     const PassParams *params;
+    const int8_t *branch_logl, *branch_lines, *branch_kind;  // per branch: log2 L, lines per tile, kind
     unsigned int *ctrl;  // ctrl[0] = next work item, ctrl[1 + i] = done counter i
     const float *in;
     float *out;
     int *err;
     long long spin_limit;
     int32_t n_items;
+    int32_t pf_ahead;  // a CTA that takes item i asks L2 for the input of item i + pf_ahead (0 = off)
 };
+
+// Ask L2 for the HBM input of a work item (single-pass rows or a four-step column band),
+// one prefetch per 32-byte sector; the CTA that takes the item about one wave later then
+// finds it in L2. Pass-2 tiles read the workspace, which is still in L2: nothing to fetch.
+__device__ __forceinline__ void prefetch_item(const PersArgs &a, const WorkItem &it) {
+    const int kind = a.branch_kind[it.branch];
+    if (kind == KIND_ROWST) return;
+    const PassParams &p = a.params[it.param];
+    const char *in = reinterpret_cast<const char *>(p.in);
+    if (p.in_user) in = reinterpret_cast<const char *>(a.in) + (intptr_t)p.in;
+    const int L = 1 << a.branch_logl[it.branch], C = a.branch_lines[it.branch];
+    const int64_t g0 = (int64_t)it.tile * C;
+    if (kind == KIND_ROWS) {  // C indexed lines of L contiguous elements
+        const int spl = L * 8 / 32;
+        for (int i = threadIdx.x; i < C * spl; i += blockDim.x) {
+            const int64_t g = g0 + i / spl;
+            if (g < p.total_lines) prefetch_l2(in + __ldg(p.line_off + g) * 8 + (i % spl) * 32);
+        }
+    } else {  // L rows of C adjacent columns at element stride in_elem
+        const int spr = (C * 8 + 31) / 32;
+        const int64_t base = (g0 >> p.log_lpt) * p.in_tr + (g0 & ((int64_t(1) << p.log_lpt) - 1)) * p.in_line;
+        for (int i = threadIdx.x; i < L * spr; i += blockDim.x)
+            prefetch_l2(in + (base + (int64_t)(i / spr) * p.in_elem) * 8 + (i % spr) * 32);
+    }
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
     unsigned int v;
@@ -115,6 +142,7 @@ __global__ void __launch_bounds__(kUnevenThreads, 3) k_uneven(const __grid_const
         const int idx = s_idx;
         if (idx >= a.n_items) break;
         const WorkItem it = a.items[idx];
+        if (a.pf_ahead > 0 && idx + a.pf_ahead < a.n_items) prefetch_item(a, a.items[idx + a.pf_ahead]);
         if (it.wait_idx >= 0) {
             if (threadIdx.x == 0) {
                 long long spins = 0;
@@ -157,6 +185,7 @@ struct UnevenState {
     std::vector<PassParams> params;
     WorkItem *d_items = nullptr;
     PassParams *d_params = nullptr;
+    int8_t *d_branch = nullptr;  // per branch: log2 L, lines per tile, kind (3 x kNumBranches)
     unsigned int *d_ctrl = nullptr;
     int n_ctrl = 0;
     int grid = 0, smem = 0;
@@ -223,6 +252,9 @@ static cudaError_t build_graph(UnevenState *u, int *d_err, cudaStream_t st) {
     if ((e = cudaGraphAddMemsetNode(&mnode, u->graph, nullptr, 0, &mp)) != cudaSuccess) return e;
     u->args.items = u->d_items;
     u->args.params = u->d_params;
+    u->args.branch_logl = u->d_branch;
+    u->args.branch_lines = u->d_branch + kNumBranches;
+    u->args.branch_kind = u->d_branch + 2 * kNumBranches;
     u->args.ctrl = u->d_ctrl;
     u->args.err = d_err;
     u->args.n_items = (int32_t)u->items.size();
@@ -400,6 +432,17 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
             const float2 *d_lo = (const float2 *)d;
             if (plan_upload(p, hi.data(), hi.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
             const float2 *d_hi = (const float2 *)d;
+            // the whole inter-pass diagonal of this length in pass-1 layout (entry t' K + b =
+            // w_n^(b t'), one rounding), shared by every row of the class
+            std::vector<float2> full((size_t)nn);
+            for (int64_t tp = 0; tp < M; ++tp)
+                for (int64_t bb = 0; bb < K; ++bb) {
+                    double cc, ss;
+                    unit_root(tp * bb, nn, &cc, &ss);
+                    full[(size_t)(tp * K + bb)] = make_float2((float)cc, (float)-ss);
+                }
+            if (plan_upload(p, full.data(), full.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+            const float2 *d_full = (const float2 *)d;
             for (int64_t id : ids) {
                 const int conj = dir[id] == 1 ? 1 : 0;
                 PassParams a{};
@@ -414,6 +457,7 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
                 a.tw = tw1;
                 a.tw2_lo = d_lo;
                 a.tw2_hi = d_hi;
+                a.tw2_full = d_full;
                 a.log_n2 = logn;
                 a.tw2_lo_bits = lob;
                 a.conj_in = conj;
@@ -466,6 +510,16 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
     if (plan_upload(p, u->params.data(), u->params.size() * sizeof(PassParams), &d) != cudaSuccess)
         return FFTC_ERR_ALLOC;
     u->d_params = (PassParams *)d;
+    {
+        std::vector<int8_t> bt(3 * kNumBranches);
+        for (int i = 0; i < kNumBranches; ++i) {
+            bt[i] = (int8_t)kBranches[i].logl;
+            bt[kNumBranches + i] = (int8_t)std::min(kBranches[i].lines, 127);
+            bt[2 * kNumBranches + i] = (int8_t)kBranches[i].kind;
+        }
+        if (plan_upload(p, bt.data(), bt.size(), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+        u->d_branch = (int8_t *)d;
+    }
     if (plan_alloc(p, (size_t)u->n_ctrl * sizeof(unsigned int), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
     u->d_ctrl = (unsigned int *)d;
     if (plan_alloc(p, 16, &d) != cudaSuccess) return FFTC_ERR_ALLOC;
@@ -484,6 +538,7 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return FFTC_ERR_CUDA;
     u->grid = std::max(1, per_sm) * sms;
     u->args.spin_limit = (long long)env_int("FFTC_SPIN_LIMIT", 20000000);
+    u->args.pf_ahead = env_int("FFTC_UNEVEN_PF", 0) ? u->grid : 0;  // measured slower: off by default
     if (build_graph(u, p->d_err, nullptr) != cudaSuccess) return FFTC_ERR_CUDA;
     return FFTC_OK;
 }

@@ -111,3 +111,64 @@ def test_uneven_rejects_bad_descriptors():
     with pytest.raises(nat.FftcError) as ei:   # overlapping rows
         fc.UnevenPlan(np.array([64, 64]), np.array([-1, -1]), np.array([0, 32]))
     assert ei.value.status == nat.ERR_INVALID_VALUE
+
+
+_CACHE_CHILD = r"""
+import os, sys
+import numpy as np
+import torch
+sys.path.insert(0, os.getcwd())
+import paper_2308_00497_gb300 as fc
+import synthetic_inputs as si
+n = np.array([1 << 13] * 3 + [1 << 15] * 3 + [256] * 5, dtype=np.int64)
+d = np.array([-1, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1], dtype=np.int8)
+o = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+total = int(o[-1] + n[-1])
+x = si.uniform_complex(1, total, seed=31).reshape(total)
+p = fc.UnevenPlan(n, d, o)
+y = p.execute(torch.from_numpy(x).cuda())
+torch.cuda.synchronize()
+p.check()
+np.save(sys.argv[1], y.cpu().numpy())
+"""
+
+
+def _cache_run(tmp_path, cache, tag):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = tmp_path / f"y_{tag}.npy"
+    env = dict(os.environ, FFTC_TUNE="1", FFTC_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", _CACHE_CHILD, str(out)], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return np.load(out)
+
+
+def test_tune_cache_file_round_trip(tmp_path):
+    """FFTC_TUNE_CACHE carries the autotuner's per-class choices across processes: a first
+    process times the candidate splits of the 2^13 and 2^15 classes and appends its choices;
+    a second process reads them back and builds the same plan (bit-identical output); an
+    entry appended to the file by hand is honoured (another split: different rounding,
+    still within tolerance of the oracle)."""
+    cache = tmp_path / "tune.txt"
+    y1 = _cache_run(tmp_path, cache, "first")
+    lines = [ln.split() for ln in cache.read_text().splitlines() if ln.startswith("uneven ")]
+    chosen = {int(t[-2].split("|")[-1]): int(t[-1]) for t in lines}
+    assert {13, 15} <= set(chosen)
+    y2 = _cache_run(tmp_path, cache, "second")
+    assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
+    dev = " ".join(lines[0][1:-1]).rsplit("|", 1)[0]  # "uneven <device name>|<log n> <log m>"
+    other = 8 if chosen[15] == 7 else 7
+    with open(cache, "a") as f:
+        f.write(f"uneven {dev}|15 {other}\n")
+    y3 = _cache_run(tmp_path, cache, "edited")
+    n = np.array([1 << 13] * 3 + [1 << 15] * 3 + [256] * 5, dtype=np.int64)
+    d = np.array([-1, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1], dtype=np.int8)
+    o = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    total = int(o[-1] + n[-1])
+    x = si.uniform_complex(1, total, seed=31).reshape(total)
+    _check_rows(x, y3, n, d, o, range(len(n)))
+    r15 = slice(int(o[3]), int(o[6]))
+    assert not np.array_equal(y1[r15].view(np.uint32), y3[r15].view(np.uint32))
