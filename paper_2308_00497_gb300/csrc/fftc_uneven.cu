@@ -33,7 +33,9 @@ namespace fftc {
 
 // (id, LOGL, LOGE, C, KIND, IDX, LOGX): every branch has C * 2^(LOGL - LOGE) = 256
 // threads; the four-step branches carry their element stride 2^LOGX at compile time
-// (one pair per split n = M K of the classes 2^13 .. 2^16).
+// (one pair per split n = M K of the classes 2^13 .. 2^16). Branches 19.. are the "half"
+// variants: half the elements per thread, so twice the threads per line, half the lines
+// per tile and one more radix stage (the autotuner's tile-shape / stages-per-pass choice).
 #define FFTC_UNEVEN_BRANCHES(X)                \
     X(0, 6, 4, 64, KIND_ROWS, true, 0)         \
     X(1, 7, 4, 32, KIND_ROWS, true, 0)         \
@@ -53,7 +55,23 @@ namespace fftc {
     X(15, 7, 3, 16, KIND_ROWST, false, 7)      \
     X(16, 8, 4, 16, KIND_ROWST, false, 7)      \
     X(17, 7, 3, 16, KIND_ROWST, false, 8)      \
-    X(18, 8, 4, 16, KIND_ROWST, false, 8)
+    X(18, 8, 4, 16, KIND_ROWST, false, 8)      \
+    X(19, 6, 3, 32, KIND_ROWS, true, 0)        \
+    X(20, 7, 3, 16, KIND_ROWS, true, 0)        \
+    X(21, 8, 3, 8, KIND_ROWS, true, 0)         \
+    X(22, 9, 3, 4, KIND_ROWS, true, 0)         \
+    X(23, 10, 3, 2, KIND_ROWS, true, 0)        \
+    X(24, 11, 3, 1, KIND_ROWS, true, 0)        \
+    X(25, 7, 2, 8, KIND_COLS, false, 6)        \
+    X(26, 7, 2, 8, KIND_COLS, false, 7)        \
+    X(27, 7, 2, 8, KIND_COLS, false, 8)        \
+    X(28, 8, 3, 8, KIND_COLS, false, 7)        \
+    X(29, 8, 3, 8, KIND_COLS, false, 8)        \
+    X(30, 7, 2, 8, KIND_ROWST, false, 6)       \
+    X(31, 7, 2, 8, KIND_ROWST, false, 7)       \
+    X(32, 7, 2, 8, KIND_ROWST, false, 8)       \
+    X(33, 8, 3, 8, KIND_ROWST, false, 7)       \
+    X(34, 8, 3, 8, KIND_ROWST, false, 8)
 
 #define FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX) \
     Pass<LOGL, LOGE, C, KIND, LAYOUT_IL, LAYOUT_IL, IDX, LOGX>
@@ -205,9 +223,19 @@ static int find_branch(int kind, int logl, int loge, int lines, int logx = 0) {
     return -1;
 }
 
-// Configuration of one length class: single pass (logm = 0) or four-step (logm > 0).
+// Configuration of one length class: single pass (logm = 0) or four-step (logm > 0), with
+// the default elements per thread (ev = 0) or half of them (ev = 1: twice the threads per
+// line, half the lines per tile, one more radix stage). Passed around as one int code.
 struct ClassCfg {
     int logm = 0;  // four-step split n = 2^logm * 2^(logn - logm); 0 = single pass
+    int ev = 0;
+    static ClassCfg decode(int code) {
+        ClassCfg c;
+        c.logm = code & 0xff;
+        c.ev = code >> 8;
+        return c;
+    }
+    int code() const { return logm | (ev << 8); }
 };
 
 static int env_int(const char *name, int dflt) {
@@ -216,14 +244,19 @@ static int env_int(const char *name, int dflt) {
 }
 
 
-static int rows_branch(int logn) { return find_branch(KIND_ROWS, logn, 4, 256 >> (logn - 4)); }
-static int cols_branch(int logm, int logk) { return find_branch(KIND_COLS, logm, logm - 4, 16, logk); }
-static int rowst_branch(int logk, int logm) { return find_branch(KIND_ROWST, logk, logk - 4, 16, logm); }
+static int rows_branch(int logn, int ev) {
+    const int loge = 4 - ev;
+    return logn > loge ? find_branch(KIND_ROWS, logn, loge, 256 >> (logn - loge)) : -1;
+}
+static int cols_branch(int logm, int logk, int ev) { return find_branch(KIND_COLS, logm, logm - 4 - ev, 16 >> ev, logk); }
+static int rowst_branch(int logk, int logm, int ev) {
+    return find_branch(KIND_ROWST, logk, logk - 4 - ev, 16 >> ev, logm);
+}
 
 static bool class_supported(int logn, const ClassCfg &c) {
-    if (c.logm == 0) return rows_branch(logn) >= 0;
+    if (c.logm == 0) return rows_branch(logn, c.ev) >= 0;
     const int logk = logn - c.logm;
-    return cols_branch(c.logm, logk) >= 0 && rowst_branch(logk, c.logm) >= 0;
+    return cols_branch(c.logm, logk, c.ev) >= 0 && rowst_branch(logk, c.logm, c.ev) >= 0;
 }
 
 int uneven_max_logn(const fftc_plan_s *p) { return p->uneven ? p->uneven->max_logn : 0; }
@@ -344,8 +377,9 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
     int64_t ws_elems = 0;
     std::map<int, ClassCfg> cfg;
     for (auto &kv : by_log) {
-        ClassCfg c;
-        c.logm = choose(kv.first, ctx);
+        const int code = choose(kv.first, ctx);
+        if (code < 0) return FFTC_ERR_UNSUPPORTED_SIZE;
+        const ClassCfg c = ClassCfg::decode(code);
         if (!class_supported(kv.first, c)) return FFTC_ERR_UNSUPPORTED_SIZE;
         cfg[kv.first] = c;
         if (c.logm) ws_elems += (int64_t(1) << kv.first) * (int64_t)kv.second.size();
@@ -378,7 +412,7 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
         const ClassCfg &c = cfg[logn];
         const int64_t nn = int64_t(1) << logn;
         if (c.logm == 0) {
-            const int b = rows_branch(logn);
+            const int b = rows_branch(logn, c.ev);
             const BranchInfo &bi = kBranches[b];
             std::vector<int64_t> loff(ids.size());
             std::vector<int8_t> lconj(ids.size());
@@ -409,7 +443,7 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
         } else {
             const int logm = c.logm, logk = logn - logm;
             const int64_t M = int64_t(1) << logm, K = int64_t(1) << logk;
-            const int b1 = cols_branch(logm, logk), b2 = rowst_branch(logk, logm);
+            const int b1 = cols_branch(logm, logk, c.ev), b2 = rowst_branch(logk, logm, c.ev);
             float2 *tw1 = nullptr, *tw2 = nullptr;
             fftc_status s = stage_table(logm, kBranches[b1].loge, &tw1);
             if (s != FFTC_OK) return s;
@@ -479,7 +513,7 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
                 const int pb = (int)u->params.size();
                 u->params.push_back(b);
                 const int done = n_done++;
-                const int64_t t1 = K / 16, t2 = M / 16;
+                const int64_t t1 = K / kBranches[b1].lines, t2 = M / kBranches[b2].lines;
                 for (int64_t t = 0; t < t1; ++t) p1.push_back(WorkItem{b1, pa, (int32_t)t, -1, 0, done});
                 queued_bytes += 8.0 * nn;
                 Pending pd;
@@ -550,17 +584,21 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
 // an optional file that carries the choices across processes)
 // ---------------------------------------------------------------------------
 static std::mutex g_tune_mu;
-static std::map<std::pair<std::string, int>, int> g_tuned;  // (device name, log n) -> log m
+static std::map<std::pair<std::string, int>, int> g_tuned;  // (device name, log n) -> class code
 static bool g_tune_file_read = false;
 
+// every compiled configuration of a length class: the split (single pass or n = M K) and the
+// elements per thread (which fix the tile shape and the stages per pass)
 static std::vector<int> candidates(int logn) {
     std::vector<int> c;
     for (int logm = 0; logm <= 8; ++logm) {
         if (logm > 0 && logm < 6) continue;
-        ClassCfg cc;
-        cc.logm = logm;
-        if (logm == 0 || (logn - logm >= 6 && logn - logm <= 8)) {
-            if (class_supported(logn, cc)) c.push_back(logm);
+        if (logm > 0 && (logn - logm < 6 || logn - logm > 8)) continue;
+        for (int ev = 0; ev <= 1; ++ev) {
+            ClassCfg cc;
+            cc.logm = logm;
+            cc.ev = ev;
+            if (class_supported(logn, cc)) c.push_back(cc.code());
         }
     }
     return c;
@@ -572,14 +610,14 @@ static int fixed_choice(int logn, void *ctx) {
 }
 
 // Time one candidate: `rows` contiguous rows of length 2^logn, forward, 64 MiB in.
-static double time_candidate(int device, int logn, int logm, void *d_in, void *d_out, int64_t rows) {
+static double time_candidate(int device, int logn, int code, void *d_in, void *d_out, int64_t rows) {
     fftc_plan_s tp;
     tp.magic = FFTC_PLAN_MAGIC;
     tp.device = device;
     std::vector<int64_t> n((size_t)rows, int64_t(1) << logn), off((size_t)rows);
     std::vector<int8_t> dir((size_t)rows, -1);
     for (int64_t i = 0; i < rows; ++i) off[(size_t)i] = i << logn;
-    int choice = logm;
+    int choice = code;
     double best = -1.0;
     if (build_state(&tp, rows, n.data(), dir.data(), off.data(), fixed_choice, &choice) == FFTC_OK) {
         cudaStream_t st;
@@ -614,18 +652,25 @@ static void read_tune_file(const std::string &dev) {
     FILE *f = fopen(path, "r");
     if (!f) return;
     char name[256];
-    int logn, logm;
-    while (fscanf(f, " uneven %255[^|]|%d %d", name, &logn, &logm) == 3)
-        if (dev == name) g_tuned[std::make_pair(dev, logn)] = logm;
+    int logn, logm, ev;
+    while (fscanf(f, " uneven %255[^|]|%d %d %d", name, &logn, &logm, &ev) == 4)
+        if (dev == name) {
+            ClassCfg c;
+            c.logm = logm;
+            c.ev = ev;
+            g_tuned[std::make_pair(dev, logn)] = c.code();
+        }
     fclose(f);
 }
 
-static void append_tune_file(const std::string &dev, int logn, int logm) {
+// one line per choice: "uneven <device name>|<log2 n> <log2 M (0: one pass)> <half-E variant>"
+static void append_tune_file(const std::string &dev, int logn, int code) {
     const char *path = getenv("FFTC_TUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "uneven %s|%d %d\n", dev.c_str(), logn, logm);
+    const ClassCfg c = ClassCfg::decode(code);
+    fprintf(f, "uneven %s|%d %d %d\n", dev.c_str(), logn, c.logm, c.ev);
     fclose(f);
 }
 
@@ -641,7 +686,9 @@ static int tuned_choice(int logn, void *vctx) {
     char name[64];
     snprintf(name, sizeof(name), "FFTC_UNEVEN_LOGM_%d", logn);
     const int forced = env_int(name, -1);
-    if (forced >= 0) return forced;
+    snprintf(name, sizeof(name), "FFTC_UNEVEN_EV_%d", logn);
+    const int forced_ev = env_int(name, 0);
+    if (forced >= 0) return forced | (forced_ev << 8);
     std::vector<int> cand = candidates(logn);
     if (cand.empty()) return -1;
     const int dflt = logn <= 12 ? 0 : logn / 2;

@@ -154,15 +154,16 @@ def test_tune_cache_file_round_trip(tmp_path):
     still within tolerance of the oracle)."""
     cache = tmp_path / "tune.txt"
     y1 = _cache_run(tmp_path, cache, "first")
+    # "uneven <device name>|<log2 n> <log2 M, 0 for one pass> <half-elements-per-thread variant>"
     lines = [ln.split() for ln in cache.read_text().splitlines() if ln.startswith("uneven ")]
-    chosen = {int(t[-2].split("|")[-1]): int(t[-1]) for t in lines}
+    chosen = {int(t[-3].split("|")[-1]): (int(t[-2]), int(t[-1])) for t in lines}
     assert {13, 15} <= set(chosen)
     y2 = _cache_run(tmp_path, cache, "second")
     assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
-    dev = " ".join(lines[0][1:-1]).rsplit("|", 1)[0]  # "uneven <device name>|<log n> <log m>"
-    other = 8 if chosen[15] == 7 else 7
+    dev = " ".join(lines[0][1:-2]).rsplit("|", 1)[0]
+    other = 8 if chosen[15][0] == 7 else 7
     with open(cache, "a") as f:
-        f.write(f"uneven {dev}|15 {other}\n")
+        f.write(f"uneven {dev}|15 {other} 0\n")
     y3 = _cache_run(tmp_path, cache, "edited")
     n = np.array([1 << 13] * 3 + [1 << 15] * 3 + [256] * 5, dtype=np.int64)
     d = np.array([-1, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1], dtype=np.int8)
