@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <map>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "fftc_mixed.cuh"
+#include "fftc_mixed_ct.cuh"
 #include "fftc_plan.h"
 
 namespace fftc {
@@ -66,6 +68,11 @@ int64_t mixed_split(int64_t n, bool fp64) {
 // 3 x 5 = 15 and 3 x 3 = 9 first, then the remaining 3, 5, 7, the power-of-two remainder
 // (2, 4 or 8), folded into one leftover odd factor where the product stays <= 16 (6, 10,
 // 14, 12), and the radix-16 stages last, where Ns is largest.
+static int getenv_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return (v && *v) ? atoi(v) : dflt;
+}
+
 static std::vector<int> mixed_radices(int64_t L) {
     int e[8] = {0};
     int64_t m = L;
@@ -189,6 +196,11 @@ static fftc_status mixed_pass_setup(fftc_plan_s *p, MixedPass &mp, int64_t L, in
     mp.threads = nt;
     mp.kernel = mixed_kernel(kind, lin, lout, nt, fp64);
     if (!mp.kernel) return FFTC_ERR_UNSUPPORTED_SIZE;
+    // the per-length kernel of this exact shape, where one is compiled (FP32)
+    if (!fp64 && getenv_int("FFTC_MIXED_CT", 1)) {
+        const MixedCtEntry *ct = find_mixed_ct(kind, lin, lout, nt, (int)L, C, a.pitch, a.nst, a.radix);
+        if (ct) mp.kernel = ct->kernel;
+    }
     mp.smem = (((C * a.pitch + 1) & ~1) + C * a.pitch) * (int)(fp64 ? sizeof(double2) : sizeof(float2));
     if (mp.smem > 48 * 1024) {
         // the dynamic shared memory of one kernel differs from plan to plan: allow the

@@ -223,18 +223,31 @@ __device__ __forceinline__ void dft_small(V *v) {
 // at one position (coalesced for column access: the four-step pass 1 reads and writes, and
 // pass 2's transposed writes); else consecutive positions of one line. KIND_COLS multiplies
 // its output by the inter-pass diagonal (when the plan has one).
+// CT_L > 0: the line length, lines per tile (CT_C), line pitch in shared memory (CT_P) and
+// this stage's Ns (CT_NS) are compile-time constants (the per-length kernels of
+// k_mixed_ct): every division, index product and loop bound of the stage is then resolved
+// by the compiler.
 template <int R, int NT, typename V, int IO = 0, int LIN = LAYOUT_IL, int LOUT = LAYOUT_IL, int KIND = KIND_ROWS,
-          bool CF = false>
+          bool CF = false, int CT_L = 0, int CT_C = 0, int CT_NS = 0, int CT_P = 0>
 __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *src, V *dst, int64_t g0 = 0) {
     using S = typename CplxT<V>::S;
     const PassParams &p = a.p;
-    const int L = a.L, Lr = L / R, Ns = a.ns[s];
-    const int G = a.C * Lr;
+    const int L = CT_L ? CT_L : a.L, Lr = L / R, Ns = CT_L ? CT_NS : a.ns[s];
+    const int C = CT_L ? CT_C : a.C, pitch = CT_L ? CT_P : a.pitch;
+    const int G = C * Lr;
     const V *tw = reinterpret_cast<const V *>(p.tw) + a.tw_off[s];
 #pragma unroll 2
     for (int gi = threadIdx.x; gi < G; gi += NT) {
         int c, j;
-        if constexpr (CF) {
+        if constexpr (CT_L > 0) {
+            if constexpr (CF) {
+                j = gi / C;
+                c = gi - j * C;
+            } else {
+                c = gi / Lr;
+                j = gi - c * Lr;
+            }
+        } else if constexpr (CF) {
             j = (int)fdiv((uint32_t)gi, a.div_C);
             c = gi - j * a.C;
         } else {
@@ -269,11 +282,11 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
                 v[t] = x;
             }
         } else {
-            const V *line = src + c * a.pitch;
+            const V *line = src + c * pitch;
 #pragma unroll
             for (int t = 0; t < R; ++t) v[t] = line[j + t * Lr];
         }
-        const int jq = (int)fdiv((uint32_t)j, a.div_ns[s]);
+        const int jq = CT_L ? j / Ns : (int)fdiv((uint32_t)j, a.div_ns[s]);
         const int jm = j - jq * Ns;
         if (Ns > 1) {
 #pragma unroll
@@ -311,7 +324,7 @@ __device__ __forceinline__ void mixed_stage(const MixedArgs &a, int s, const V *
                 }
             }
         } else {
-            V *out = dst + c * a.pitch;
+            V *out = dst + c * pitch;
 #pragma unroll
             for (int t = 0; t < R; ++t) out[o + t * Ns] = v[t];
         }

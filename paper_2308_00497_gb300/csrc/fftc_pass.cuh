@@ -103,7 +103,7 @@ struct Pass {
     static constexpr bool WARP_SYNC = all_tau() && TPL <= 32 && (32 % TPL) == 0;
     // registers per thread the launch bounds aim at: E = 32 needs ~128; E = 16 fits 80, or 64
     // for 512-thread CTAs so that two of them share an SM
-    static constexpr int REG_TARGET = E >= 32 ? 128 : (E >= 16 ? (NT >= 512 ? 64 : 80) : 64);
+    static constexpr int REG_TARGET = TC ? 64 : (E >= 32 ? 128 : (E >= 16 ? (NT >= 512 ? 64 : 80) : 64));
     static constexpr int MINB = (65536 / (NT * REG_TARGET)) > 0 ? (65536 / (NT * REG_TARGET)) : 1;
     // element strides: compile-time unless LOGX == 0 for a four-step kind
     static constexpr int ES_IN_CT = COLS_LIKE ? (LOGX ? (1 << LOGX) : 0) : 1;

@@ -154,3 +154,31 @@ def test_tuned_split_search(n, layout):
         assert rel_l2_rows(y[[0, B - 1]], ref).max() <= tol_fp32(n)
         splits.add((m, k))
     assert len(splits) == 1
+
+
+CT_SINGLE = [12, 96, 360, 1000, 3072, 6000]
+CT_TWO = [10000, 59049, 100000, 1000000]
+
+
+@pytest.mark.parametrize("n", CT_SINGLE + CT_TWO)
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_per_length_kernels(monkeypatch, n, layout, inverse):
+    """The per-length (compile-time radix schedule) kernels against the oracle, both layouts
+    and directions, with a batch whose last tile is partial; the runtime-radix kernel of the
+    same plan (FFTC_MIXED_CT=0) agrees with them to the FP32 tolerance."""
+    import paper_2308_00497_gb300 as fc
+    B = {12: 345, 96: 43, 360: 11}.get(n, 3)
+    x = si.uniform_complex(B, n, seed=n + 7)
+    rows = np.array([0, B - 1]) if n >= 10000 else np.arange(B)
+    ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
+    outs = []
+    for ct in ("1", "0"):
+        monkeypatch.setenv("FFTC_MIXED_CT", ct)
+        p = fc.Plan(n, B, layout, inverse)
+        y = from_device(p.execute(to_device(x, layout)), layout)
+        torch.cuda.synchronize()
+        p.check()
+        assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n), (n, layout, inverse, ct)
+        outs.append(y)
+    assert rel_l2_rows(outs[0], outs[1].astype(np.complex128)).max() <= 2 * tol_fp32(n)
