@@ -251,7 +251,7 @@ def run_fftc(args, rank: int, world: int, local_rank: int) -> None:
             for inv in args.dirs:
                 pl = fc.Plan(n, B, layout, inv, precision=args.precision, device=dev)
                 if args.tune:
-                    pl.tune(3)  # measure-mode planning, outside the timed region
+                    pl.tune(5)  # measure-mode planning, outside the timed region
                 plans.append((e, layout, inv, pl))
 
     def views(layout, n, B):
@@ -412,8 +412,32 @@ def run_extras(args, dev) -> dict:
     from paper_2308_00497_gb300.autograd import spectral_filter
     out = {}
     reps = max(3, args.steps)
+    sel = set(args.extras.split(","))
+    if "uneven" in sel:
+        out["uneven"] = run_uneven(args, dev, reps)
+    if "filter" in sel:
+        out["spectral_filter"] = run_filter(dev, reps)
+    if "mixed" in sel:
+        out["mixed_radix"] = run_mixed(dev, reps)
+    if "large" in sel:
+        out["large_n"] = run_large(dev, reps)
+    if "nd" in sel:
+        out["multidim"] = run_nd(dev, reps)
+    if "fp64" in sel:
+        out["fp64"] = run_fp64(dev, reps)
+    if "precision" in sel and not args.no_precision:
+        out["precision"] = run_precision(args, dev, reps)
+    return out
 
-    # uneven batch: 4096 rows, n = 2^6..2^16 log-uniform, mixed directions, one launch
+
+def run_uneven(args, dev, reps: int) -> dict:
+    """Uneven batch: 4096 rows, n = 2^6..2^16 log-uniform, mixed directions, one persistent
+    launch, against one uniform batched plan per (n, direction) class launched separately
+    (measure-mode planned when the bench tunes)."""
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    import synthetic_inputs as si
     n, d, o, total = si.uneven_batch(4096, seed=4)
     x = torch.from_numpy(si.uneven_data(total, seed=4)).to(dev)
     y = torch.empty_like(x)
@@ -428,20 +452,29 @@ def run_extras(args, dev) -> dict:
     for (v, dd), cnt in classes.items():
         xb = torch.zeros((cnt, v), dtype=torch.complex64, device=dev)
         bufs.append((xb, torch.empty_like(xb)))
-        plans.append(fc.Plan(v, cnt, "interleaved", dd == 1, device=dev))
+        pl = fc.Plan(v, cnt, "interleaved", dd == 1, device=dev)
+        plans.append(pl.tune(3) if args.tune else pl)
     def per_class():
         for (xb, yb), p in zip(bufs, plans):
             p.execute(xb, yb)
     t_sep = _time_ms(per_class, reps)
-    out["uneven"] = {"workload": "4096 rows, n=2^6..2^16 log-uniform, mixed fwd/inv, interleaved, one persistent "
-                                 "launch from a CUDA graph", "elements": int(total), "ms": round(t_uneven, 4),
-                     "gflops": round(fl / (t_uneven * 1e-3) / 1e9, 1),
-                     "hbm_frac_strict": round(16.0 * total / (t_uneven * 1e-3) / 1e9 / peaks()[0], 4),
-                     "separate_launches_ms": round(t_sep, 4), "separate_launches": len(plans),
-                     "speedup_vs_separate": round(t_sep / t_uneven, 3)}
+    res = {"workload": "4096 rows, n=2^6..2^16 log-uniform, mixed fwd/inv, interleaved, one persistent "
+                       "launch from a CUDA graph", "elements": int(total), "ms": round(t_uneven, 4),
+           "gflops": round(fl / (t_uneven * 1e-3) / 1e9, 1),
+           "hbm_frac_strict": round(16.0 * total / (t_uneven * 1e-3) / 1e9 / peaks()[0], 4),
+           "separate_launches_ms": round(t_sep, 4), "separate_launches": len(plans),
+           "speedup_vs_separate": round(t_sep / t_uneven, 3)}
     del bufs, plans, x, y
+    return res
 
-    # differentiation: batched spectral filter forward + backward, [1024, 2^14]
+
+def run_filter(dev, reps: int) -> dict:
+    """Differentiation: batched spectral filter forward + backward, [1024, 2^14]."""
+    import torch
+
+    import paper_2308_00497_gb300 as fc
+    import synthetic_inputs as si
+    from paper_2308_00497_gb300.autograd import spectral_filter
     B, nn = 1024, 1 << 14
     xs = torch.from_numpy(si.gaussian_complex(B, nn, seed=5)).to(dev).requires_grad_(True)
     ts = torch.from_numpy(si.gaussian_complex(B, nn, seed=55)).to(dev)
@@ -465,19 +498,13 @@ def run_extras(args, dev) -> dict:
         fp.execute_pointwise(uf, H, 1.0 / nn, out=gf)
         ip.execute(gf, gf)
     t_lib = _time_ms(lib_only, reps)
-    out["spectral_filter"] = {"workload": "y = ifft(H * fft(x)) / n, loss ||y - t||^2, x,t [1024, 2^14] complex64",
-                              "fwd_bwd_ms": round(t_fb, 4), "fft_ms": round(t_fft, 4),
-                              "library_ms": round(t_lib, 4), "torch_ms": round(max(t_fb - t_lib, 0.0), 4),
-                              "library_over_4_ffts": round(t_lib / (4 * t_fft), 3),
-                              "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
+    res = {"workload": "y = ifft(H * fft(x)) / n, loss ||y - t||^2, x,t [1024, 2^14] complex64",
+           "fwd_bwd_ms": round(t_fb, 4), "fft_ms": round(t_fft, 4),
+           "library_ms": round(t_lib, 4), "torch_ms": round(max(t_fb - t_lib, 0.0), 4),
+           "library_over_4_ffts": round(t_lib / (4 * t_fft), 3),
+           "fwd_bwd_over_4_ffts": round(t_fb / (4 * t_fft), 3)}
     del xs, ts, xf, uf, gf
-    out["mixed_radix"] = run_mixed(dev, reps)
-    out["large_n"] = run_large(dev, reps)
-    out["multidim"] = run_nd(dev, reps)
-    out["fp64"] = run_fp64(dev, reps)
-    if not args.no_precision:
-        out["precision"] = run_precision(args, dev, reps)
-    return out
+    return res
 
 
 FP64_SIZES = [1024, 1000, 1 << 16, 1 << 20]
@@ -640,6 +667,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the uneven / filter / precision lines")
     ap.add_argument("--no-precision", action="store_true", help="skip the tensor-core precision line")
+    ap.add_argument("--extras", default="uneven,filter,mixed,large,nd,fp64,precision",
+                    help="which secondary workloads to run (comma list)")
     ap.add_argument("--sizes", default=",".join(str(e) for e in SIZES),
                     help="log2 n list (default: the whole sweep); a subset is for profiling only")
     ap.add_argument("--layouts", default=",".join(LAYOUTS))

@@ -176,8 +176,11 @@ fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k);
  * plans: the last axis' 1D plan is tuned as above, and every strided power-of-two axis
  * keeps the faster of its compiled column pass and the runtime-radix pass. Choices are
  * cached per shape for the process, so a second plan of the same shape is tuned without
- * timing. Synchronises the device; do not call it while the plan executes. Uneven and
- * tensor-core plans are returned unchanged. reps in [1, 1000].
+ * timing; with the environment variable FFTC_TUNE_CACHE naming a file, 1D power-of-two
+ * choices are also appended to it and read back by later processes (FFTW's "wisdom").
+ * Synchronises the device; do not call it while the plan executes. Tensor-core plans choose
+ * among the kernels of their own precision mode; uneven plans are tuned when they are
+ * created (fftc_plan_create_uneven) and are returned unchanged. reps in [1, 1000].
  */
 fftc_status fftc_plan_tune(fftc_plan plan, int reps);
 

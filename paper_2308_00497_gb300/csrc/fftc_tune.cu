@@ -14,7 +14,10 @@
 // Choices are cached per (n, batch, layout, direction, precision) for the process.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <map>
+#include <string>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -34,6 +37,106 @@ struct Choice {
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int64_t, int64_t, int, int, int>, Choice> g_tune_cache;
+bool g_tune_file_read = false;
+
+// FFTC_TUNE_CACHE, when set, names a text file that carries the choices across processes
+// (FFTW's "wisdom"): one line per shape,
+//   plan <device name>|<n> <batch> <layout> <direction> <precision> S <k1>
+//   plan <device name>|<n> <batch> <layout> <direction> <precision> F <log2 M> <pf> <k1> <k2>
+//   plan <device name>|<n> <batch> <layout> <direction> <precision> C <log2 n> <log2 n1> <loge> <R> <layout>
+// with a kernel written as its registry identity "kind logl loge lines lin lout prec logx
+// pipe". Lines whose kernels this build lacks are ignored (the shape is then timed again).
+std::string device_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "";
+    return prop.name;
+}
+
+void put_kernel(std::string &out, const KernelEntry *k) {
+    char b[160];
+    snprintf(b, sizeof(b), " %d %d %d %d %d %d %d %d %d", k->kind, k->logl, k->loge, k->lines, k->lin, k->lout, k->prec,
+             k->logx, k->pipe);
+    out += b;
+}
+
+const KernelEntry *get_kernel(const char *&s) {
+    int v[9], used = 0;
+    if (sscanf(s, " %d %d %d %d %d %d %d %d %d%n", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8],
+               &used) != 9)
+        return nullptr;
+    s += used;
+    return find_kernel(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]);
+}
+
+void read_tune_file() {
+    const char *path = getenv("FFTC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    const std::string dev = device_name();
+    char line[512], name[256], kind;
+    long long n, batch;
+    int lay, dir, prec, used;
+    while (fgets(line, sizeof(line), f)) {
+        if (sscanf(line, "plan %255[^|]|%lld %lld %d %d %d %c%n", name, &n, &batch, &lay, &dir, &prec, &kind, &used) != 7 ||
+            dev != name)
+            continue;
+        const char *rest = line + used;
+        Choice c;
+        bool ok = false;
+        if (kind == 'S') {
+            ok = (c.k1 = get_kernel(rest)) != nullptr;
+        } else if (kind == 'F') {
+            int u2 = 0;
+            if (sscanf(rest, " %d %d%n", &c.logm, &c.pf1, &u2) == 2) {
+                rest += u2;
+                c.k1 = get_kernel(rest);
+                c.k2 = c.k1 ? get_kernel(rest) : nullptr;
+                ok = c.k1 && c.k2;
+            }
+        } else if (kind == 'C') {
+            int v[5];
+            if (sscanf(rest, " %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4]) == 5)
+                for (int i = 0; i < cluster_kernel_count() && !ok; ++i) {
+                    const ClusterEntry *e = cluster_kernel_at(i);
+                    if (e->logn == v[0] && e->log1 == v[1] && e->loge == v[2] && e->r == v[3] && e->lay == v[4]) {
+                        c.cl = e;
+                        ok = true;
+                    }
+                }
+        }
+        if (ok) g_tune_cache[std::make_tuple((int64_t)n, (int64_t)batch, lay, dir, prec)] = c;
+    }
+    fclose(f);
+}
+
+void append_tune_file(const std::tuple<int64_t, int64_t, int, int, int> &key, const Choice &c, int npasses) {
+    const char *path = getenv("FFTC_TUNE_CACHE");
+    if (!path || !*path) return;
+    char head[384];
+    snprintf(head, sizeof(head), "plan %s|%lld %lld %d %d %d", device_name().c_str(), (long long)std::get<0>(key),
+             (long long)std::get<1>(key), std::get<2>(key), std::get<3>(key), std::get<4>(key));
+    std::string line = head;
+    if (c.cl) {
+        char b[96];
+        snprintf(b, sizeof(b), " C %d %d %d %d %d", c.cl->logn, c.cl->log1, c.cl->loge, c.cl->r, c.cl->lay);
+        line += b;
+    } else if (npasses == 2) {
+        char b[64];
+        snprintf(b, sizeof(b), " F %d %d", c.logm, c.pf1);
+        line += b;
+        put_kernel(line, c.k1);
+        put_kernel(line, c.k2);
+    } else {
+        line += " S";
+        put_kernel(line, c.k1);
+    }
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s\n", line.c_str());
+    fclose(f);
+}
 
 struct Scratch {
     void *in = nullptr, *out = nullptr;
@@ -258,6 +361,10 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
     std::map<std::pair<int, int>, const float2 *> tabs;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (!g_tune_file_read) {
+            read_tune_file();
+            g_tune_file_read = true;
+        }
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) return apply(p, it->second, tabs);
     }
@@ -342,6 +449,7 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
     if (st != FFTC_OK) return st;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
+    append_tune_file(key, best, p->npasses);
     return FFTC_OK;
 }
 

@@ -651,10 +651,10 @@ static void read_tune_file(const std::string &dev) {
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char name[256];
+    char line[512], name[256];
     int logn, logm, ev;
-    while (fscanf(f, " uneven %255[^|]|%d %d %d", name, &logn, &logm, &ev) == 4)
-        if (dev == name) {
+    while (fgets(line, sizeof(line), f))  // the file also holds other planners' lines
+        if (sscanf(line, "uneven %255[^|]|%d %d %d", name, &logn, &logm, &ev) == 4 && dev == name) {
             ClassCfg c;
             c.logm = logm;
             c.ev = ev;

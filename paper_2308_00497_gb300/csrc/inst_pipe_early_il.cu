@@ -1,7 +1,7 @@
 // Instantiations of pipelined passes whose refill is issued after the tile's last
 // shared read (fftc_pipe.cuh, EARLY), interleaved layout: single pass n = 2^11 .. 2^14 (at 2^14
 // one 135 KB tile per SM, at 2^13 two 68 KB tiles), four-step pass 2 (one bulk copy per
-// tile) and four-step pass 1 (tensor-map boxes of 16 or 32 columns, one landing buffer).
+// tile) and four-step pass 1 (tensor-map boxes of 8, 16 or 32 columns, one landing buffer).
 #include "fftc_pipe.cuh"
 
 namespace fftc {
@@ -16,6 +16,8 @@ extern const KernelEntry kPipeEarlyIlTable[] = {
     PTE(8, 4, 16, 7, 2),  PTE(8, 4, 16, 8, 2),  PTE(9, 5, 8, 8, 2),   PTE(10, 5, 8, 8, 2),  PTE(10, 5, 8, 9, 2),
     PTE(10, 5, 8, 10, 2),
     PCE(7, 4, 16, 8, 1),  PCE(8, 4, 16, 8, 1),  PCE(8, 4, 16, 9, 1),  PCE(8, 4, 32, 10, 1), PCE(9, 4, 16, 10, 1),
+    // n = 2^20 as 2^9 x 2^11 and 2^10 x 2^10: 16 or 32 columns, 8 to 16 elements per thread
+    PCE(9, 4, 16, 11, 1), PCE(9, 4, 32, 11, 1), PCE(10, 4, 16, 10, 1), PCE(10, 5, 8, 10, 1),
 };
 extern const int kPipeEarlyIlCount = sizeof(kPipeEarlyIlTable) / sizeof(kPipeEarlyIlTable[0]);
 

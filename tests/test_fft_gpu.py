@@ -389,3 +389,59 @@ def test_cluster_landing_wait_reports_timeout(monkeypatch):
     """The cluster pass's landing waits run out with the hook: every CTA sets the error word
     and still runs its cluster barriers, so the launch ends and the status is reported."""
     _timeout_then_recover(monkeypatch, 1 << 16, 9, "split", {"FFTC_CLUSTER": "1"})
+
+
+_WISDOM_CHILD = r"""
+import os, sys, json
+import numpy as np
+import torch
+sys.path.insert(0, os.getcwd())
+import paper_2308_00497_gb300 as fc
+import synthetic_inputs as si
+n, B = 1 << 16, 64
+x = si.uniform_complex(B, n, seed=5)
+p = fc.Plan(n, B).tune(2)
+y = p.execute(torch.from_numpy(x).cuda())
+torch.cuda.synchronize()
+np.save(sys.argv[1], y.cpu().numpy())
+print(json.dumps({"split": p.split(), "info": p.info()}))
+"""
+
+
+def _wisdom_run(tmp_path, cache, tag):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = tmp_path / f"w_{tag}.npy"
+    env = dict(os.environ, FFTC_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", _WISDOM_CHILD, str(out)], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return np.load(out), json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_tune_cache_carries_plan_choices(tmp_path):
+    """FFTC_TUNE_CACHE keeps measure-mode choices across processes: the first process times the
+    candidates of a 2^16 plan and appends its choice; a second process reads it back (same split
+    and radices, bit-identical output); a line edited by hand to another split is honoured."""
+    cache = tmp_path / "wisdom.txt"
+    y1, m1 = _wisdom_run(tmp_path, cache, "first")
+    lines = [ln for ln in cache.read_text().splitlines() if ln.startswith("plan ")]
+    assert len(lines) == 1
+    y2, m2 = _wisdom_run(tmp_path, cache, "second")
+    assert m1 == m2 and np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
+    head, rest = lines[0].split("|", 1)
+    f = rest.split()
+    assert f[5] in ("S", "F", "C")
+    # a two-pass choice at the split 2^7 x 2^9 (plain column kernel: E 16, 16 lines, runtime
+    # stride; row kernel: E 32, 16 lines, runtime stride), appended after the first line
+    other = f"{head}|{' '.join(f[:5])} F 7 0 1 7 4 16 0 0 0 0 0 2 9 5 16 0 0 0 0 0"
+    with open(cache, "a") as fh:
+        fh.write(other + "\n")
+    y3, m3 = _wisdom_run(tmp_path, cache, "edited")
+    assert tuple(m3["split"]) == (128, 512)
+    x = si.uniform_complex(64, 1 << 16, seed=5)
+    ref = oracle.fft(x[[0, 63]].astype(np.complex128))
+    assert rel_l2_rows(y3[[0, 63]], ref).max() <= tol_fp32(1 << 16)
