@@ -18,6 +18,8 @@ extern const KernelEntry kPipeEarlySplitTable[] = {
     PCE(7, 4, 16, 8, 1),  PCE(8, 4, 16, 8, 1),  PCE(8, 4, 16, 9, 1),  PCE(8, 4, 32, 10, 1), PCE(9, 4, 16, 10, 1),
     // n = 2^20 as 2^9 x 2^11 and 2^10 x 2^10: 16 or 32 columns, 8 to 16 elements per thread
     PCE(9, 4, 16, 11, 1), PCE(9, 4, 32, 11, 1), PCE(10, 4, 16, 10, 1), PCE(10, 5, 8, 10, 1),
+    // 32-column boxes for n = 2^15 .. 2^17
+    PCE(7, 4, 32, 8, 1), PCE(8, 4, 32, 8, 1), PCE(8, 4, 32, 9, 1), PCE(9, 4, 32, 10, 1),
 };
 extern const int kPipeEarlySplitCount = sizeof(kPipeEarlySplitTable) / sizeof(kPipeEarlySplitTable[0]);
 

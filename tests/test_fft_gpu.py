@@ -445,3 +445,35 @@ def test_tune_cache_carries_plan_choices(tmp_path):
     x = si.uniform_complex(64, 1 << 16, seed=5)
     ref = oracle.fft(x[[0, 63]].astype(np.complex128))
     assert rel_l2_rows(y3[[0, 63]], ref).max() <= tol_fp32(1 << 16)
+
+
+@pytest.mark.parametrize("e,logm,loge,lines,p1", [
+    (15, 7, 4, 32, 0), (16, 8, 4, 32, 0), (17, 8, 4, 32, 0), (16, 8, 5, 32, 0), (17, 8, 5, 32, 0),
+    (15, 7, 4, 32, 5), (16, 8, 4, 32, 5), (17, 8, 4, 32, 5),
+    (20, 9, 4, 16, 5), (20, 9, 4, 32, 5), (20, 10, 4, 16, 5), (20, 10, 5, 8, 5),
+    (19, 9, 5, 32, 0), (20, 9, 5, 32, 0), (19, 9, 4, 32, 5),
+])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_pass1_band_variants(monkeypatch, e, logm, loge, lines, p1, layout):
+    """Every pass-1 column kernel that measure-mode planning may pick for the sweep sizes (plain
+    loads or tensor-map boxes, 8 to 32 columns, 16 or 32 elements per thread), forced through
+    the planner's knobs, against the oracle on sampled rows."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_TUNE_FOURSTEP_LOGM", str(logm))
+    monkeypatch.setenv("FFTC_TUNE_COLS_E", str(loge))
+    monkeypatch.setenv("FFTC_TUNE_COLS_C", str(lines))
+    monkeypatch.setenv("FFTC_PIPE4", "1" if p1 else "0")
+    if p1:
+        monkeypatch.setenv("FFTC_TUNE_P1_PIPE", str(p1))
+    n = 1 << e
+    B = max(3, (1 << 22) // n)
+    x = si.uniform_complex(B, n, seed=e * 7 + lines)
+    p = fc.Plan(n, B, layout, e % 2 == 0)
+    assert p.split()[0] == 1 << logm
+    assert p.info()[1][0] == 1 << loge  # pass 1 runs radix-2^loge stages
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    rows = np.array([0, B // 2, B - 1])
+    ref = oracle.fft(x[rows].astype(np.complex128), inverse=e % 2 == 0)
+    assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
