@@ -13,7 +13,7 @@
 // wait, and any pass-1 tile a pass-2 tile depends on was taken earlier by a running CTA,
 // so the waits always end. A wait that exceeds its iteration limit sets the plan's error
 // word and the tile proceeds (fftc_plan_check then reports FFTC_ERR_TIMEOUT).
-// All branches run 256-thread CTAs with E <= 16 (3 CTAs per SM).
+// All branches run 256-thread CTAs with E <= 16 (4 CTAs per SM).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -90,6 +90,10 @@ static const int kNumBranches = sizeof(kBranches) / sizeof(kBranches[0]);
 FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_CHECK)
 
 static constexpr int kUnevenThreads = 256;
+// CTAs per SM the kernel is compiled for (64 registers a thread at 4): measured on the
+// 4096-row workload, 3 (80 registers) 0.350 ms, 4 0.312 ms, 5 (48 registers, spilling)
+// 0.328 ms
+static constexpr int kUnevenCtasPerSm = 4;
 
 struct WorkItem {
     int32_t branch, param, tile;
@@ -143,22 +147,29 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
 
 // Drop the L2 lines of workspace rows a pass-2 tile has finished reading (`elems`
 // complex elements from `ws`): the workspace is never read again in this launch, so its
-// dirty lines need not be written back to HBM.
+// dirty lines need not be written back to HBM. Called after a CTA barrier that follows
+// the tile: every load of the tile has returned by then (each thread consumed its loads
+// before the tile's first exchange barrier).
 __device__ __forceinline__ void discard_rows(const float *ws, int elems) {
-    __syncthreads();  // every load of the tile has returned
     const char *base = reinterpret_cast<const char *>(ws);
     for (int o = threadIdx.x * 128; o < elems * 8; o += kUnevenThreads * 128)
         asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + o) : "memory");
 }
 
-__global__ void __launch_bounds__(kUnevenThreads, 3) k_uneven(const __grid_constant__ PersArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(kUnevenThreads, MINB) k_uneven(const __grid_constant__ PersArgs a) {
     extern __shared__ float2 sm_pers[];
-    __shared__ int s_idx;
-    for (;;) {
-        if (threadIdx.x == 0) s_idx = (int)atomicAdd(a.ctrl, 1u);
-        __syncthreads();
-        const int idx = s_idx;
+    __shared__ int s_idx[2];  // the item in hand and the item claimed after it
+    if (threadIdx.x == 0) s_idx[0] = (int)atomicAdd(a.ctrl, 1u);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const int idx = s_idx[cur];
         if (idx >= a.n_items) break;
+        // Claim the next item now, so the CTA goes straight on to it when this one ends.
+        // Claims follow the list order, so the earliest unfinished item is always the
+        // item in hand of some CTA, and every item a pass-2 tile waits for comes before
+        // it in the list: the waits still end.
+        if (threadIdx.x == 0) s_idx[cur ^ 1] = (int)atomicAdd(a.ctrl, 1u);
         const WorkItem it = a.items[idx];
         if (a.pf_ahead > 0 && idx + a.pf_ahead < a.n_items) prefetch_item(a, a.items[idx + a.pf_ahead]);
         if (it.wait_idx >= 0) {
@@ -172,26 +183,35 @@ __global__ void __launch_bounds__(kUnevenThreads, 3) k_uneven(const __grid_const
                     __nanosleep(128);
                 }
             }
-            __syncthreads();
+            __syncthreads();  // the acquire by thread 0 orders the tile's workspace loads
         }
         PassParams p = a.params[it.param];
         if (p.in_user) p.in = reinterpret_cast<const float *>(reinterpret_cast<const char *>(a.in) + (intptr_t)p.in);
         if (p.out_user) p.out = reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (intptr_t)p.out);
+        const float *ws_done = nullptr;
+        int ws_elems = 0;
         switch (it.branch) {
-#define FFTC_BRANCH_CASE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)                                       \
-    case ID:                                                                                       \
-        FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)::run_tile(p, it.tile, sm_pers);        \
-        if (KIND == KIND_ROWST) discard_rows(p.in + 2 * (int64_t)it.tile * C * (1 << LOGL), C << LOGL); \
+#define FFTC_BRANCH_CASE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)                                 \
+    case ID:                                                                                 \
+        FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX)::run_tile(p, it.tile, sm_pers);  \
+        if (KIND == KIND_ROWST) {                                                            \
+            ws_done = p.in + 2 * (int64_t)it.tile * C * (1 << LOGL);                         \
+            ws_elems = C << LOGL;                                                            \
+        }                                                                                    \
         break;
             FFTC_UNEVEN_BRANCHES(FFTC_BRANCH_CASE)
             default: break;
         }
-        if (it.signal_idx >= 0) {
-            __threadfence();  // this thread's stores are visible device-wide ...
-            __syncthreads();  // ... before thread 0 signals for the whole CTA
-            if (threadIdx.x == 0) atomicAdd(a.ctrl + 1 + it.signal_idx, 1u);
+        // One barrier ends the item: every thread's stores of the tile are issued, its
+        // shared memory may be reused, and the claim of the next item is visible.
+        __syncthreads();
+        if (ws_elems) discard_rows(ws_done, ws_elems);
+        if (it.signal_idx >= 0 && threadIdx.x == 0) {
+            // after the barrier, thread 0's device-scope fence orders the whole CTA's stores
+            // of the tile before the counter increment that releases its pass-2 tiles
+            __threadfence();
+            atomicAdd(a.ctrl + 1 + it.signal_idx, 1u);
         }
-        __syncthreads();  // s_idx and shared memory are reused by the next item
     }
 }
 
@@ -210,6 +230,7 @@ struct UnevenState {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t knode = nullptr;
+    void *kfunc = nullptr;  // the k_uneven instance
     PersArgs args{};
     int max_logn = 0;
     int64_t total_elems = 0;
@@ -295,7 +316,7 @@ static cudaError_t build_graph(UnevenState *u, int *d_err, cudaStream_t st) {
     u->args.out = nullptr;
     void *kargs[] = {&u->args};
     cudaKernelNodeParams kp{};
-    kp.func = (void *)k_uneven;
+    kp.func = u->kfunc;
     kp.gridDim = dim3(u->grid);
     kp.blockDim = dim3(kUnevenThreads);
     kp.sharedMemBytes = u->smem;
@@ -311,7 +332,7 @@ fftc_status uneven_run(fftc_plan_s *p, const void *in, void *out, cudaStream_t s
         u->args.out = (float *)out;
         void *kargs[] = {&u->args};
         cudaKernelNodeParams kp{};
-        kp.func = (void *)k_uneven;
+        kp.func = u->kfunc;
         kp.gridDim = dim3(u->grid);
         kp.blockDim = dim3(kUnevenThreads);
         kp.sharedMemBytes = u->smem;
@@ -564,10 +585,11 @@ static fftc_status build_state(fftc_plan_s *p, int64_t count, const int64_t *n, 
     int smem = 0;
     for (int i = 0; i < kNumBranches; ++i) smem = std::max(smem, kBranches[i].smem);
     u->smem = smem;
-    if (cudaFuncSetAttribute(k_uneven, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    u->kfunc = (void *)k_uneven<kUnevenCtasPerSm>;
+    if (cudaFuncSetAttribute(u->kfunc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return FFTC_ERR_CUDA;
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uneven, kUnevenThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u->kfunc, kUnevenThreads, smem) != cudaSuccess)
         return FFTC_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return FFTC_ERR_CUDA;
     u->grid = std::max(1, per_sm) * sms;
