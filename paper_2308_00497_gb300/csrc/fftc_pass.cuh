@@ -287,7 +287,7 @@ struct Pass {
                     for (int t = 0; t < R; ++t) v[q * R + t] = src[t * (L / R)];
                 }
             }
-            if constexpr (H::active && s == S - 1 && !TCS) {
+            if constexpr (H::active && s == S - 1) {
                 __syncthreads();  // the last shared read of the tile is done: the buffer is free
                 hook();
             }
@@ -300,19 +300,16 @@ struct Pass {
             }
         }
         if constexpr (TCS) {
-            if constexpr (s > 0 || LANDED) __syncthreads();  // every read of the buffer the A rows alias is done
             // the i-th tensor-core stage of this CTA's k-th tile uses mbarrier phase (k NTC + i) mod 2
             const uint32_t phase = (tk * NTC + tc_count(s)) & 1u;
-            TcUnit<NT, TCM>::dft16(p, v, dyn_smem_base128(), smem_u32(sm), phase);
-            __syncthreads();  // every group's MMA has read its A rows
-            if constexpr (H::active && s == S - 1) hook();  // the tile buffer is free
+            TcUnit<NT, TCM>::dft16(p, v, dyn_smem_base128(), phase);
         } else {
 #pragma unroll
             for (int q = 0; q < E / R; ++q) dft<R>(v + q * R);
         }
 
         if constexpr (s < S - 1) {
-            if constexpr ((s > 0 || LANDED) && !TCS) sync();  // every read of this stage precedes any overwrite
+            if constexpr (s > 0 || LANDED) sync();  // every read of this stage precedes any overwrite
 #pragma unroll
             for (int q = 0; q < E / R; ++q) {
                 const int j = tau + q * TPL;

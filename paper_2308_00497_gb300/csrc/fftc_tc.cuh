@@ -17,13 +17,14 @@
 // FP16 range; the store scales back by 4 per stage. BF16 has FP32's exponent range.
 //
 // Data path of a group: the thread that owns the group in the CUDA-core pass kernel (16
-// elements in registers, twiddled in FP32) writes its row of A into shared memory (in
-// the no-swizzle K-major core-matrix layout, aliasing the tile's exchange buffer, which is
-// free at that point), one thread of the 128-thread group issues the MMAs and commits
-// them to an mbarrier, and every thread reads its row of D back from tensor memory
-// (tcgen05.ld 32x32b: warp w of the group owns lanes 32 (w mod 4) .. + 31) straight into
-// the registers where the CUDA-core butterfly would have left it. The pass kernel then
-// goes on unchanged: FP32 twiddles, shared-memory exchange, coalesced HBM store.
+// elements in registers, twiddled in FP32) writes its row of A into tensor memory with
+// tcgen05.st (lane = row; warp w of the group owns lanes 32 (w mod 4) .. + 31), one thread
+// of the 128-thread group issues the MMAs (A from tensor memory, B from shared memory) and
+// commits them to an mbarrier, and every thread reads its row of D back from tensor
+// memory (tcgen05.ld 32x32b) straight into the registers where the CUDA-core butterfly
+// would have left it. The tile's shared memory is not touched, so the stage needs no CTA
+// barrier of its own: the pass kernel goes on unchanged (FP32 twiddles, shared-memory
+// exchange, coalesced HBM store).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -48,9 +49,10 @@ __host__ __device__ constexpr bool tc_is_split(int mode) { return mode == TC_FP1
 //   [4160]        TMEM base address written by tcgen05.alloc
 constexpr int kTcAreaBytes = 4096 + 128;
 constexpr int kTcBLo = 2048, kTcBars = 4096, kTcTmem = 4096 + 64;
-// A rows of one 128-thread group: 16 row groups x 8 chunks of 16 bytes (hi re, hi im,
-// lo re, lo im: two chunks each) = 16 KB; row group g at g * 1024, chunk c at c * 128
-constexpr int kTcASbo = 1024, kTcAGroupBytes = 16 * kTcASbo;
+// Tensor memory of a 128-thread group g: 64 columns from 64 g, the FP32 D tile (32 columns:
+// 16 real then 16 imaginary outputs) then the A rows (FP16/BF16 pairs, lower K in the low
+// half: hi re, hi im, lo re, lo im, 8 columns each = K 0..15 of each part)
+constexpr uint32_t kTcGroupCols = 64, kTcACol = 32;
 
 __device__ __forceinline__ uint32_t tc_pack2(float a, float b, bool bf) {
     if (bf) {
@@ -106,10 +108,10 @@ __device__ __forceinline__ float tc_b_value(int n, int k) {
     return k < 16 ? -s : c;                        // Wi, Wr
 }
 
-// TMEM columns of a CTA of nt threads: one 32-column FP32 tile per 128-thread group,
-// rounded up to a power of two >= 32 (the allocation granule)
+// TMEM columns of a CTA of nt threads: 64 per 128-thread group (D tile and A rows), a power
+// of two (the allocation granule)
 __host__ __device__ constexpr uint32_t tc_tmem_cols(int nt) {
-    return nt <= 128 ? 32u : (nt <= 256 ? 64u : (nt <= 512 ? 128u : 256u));
+    return nt <= 128 ? 64u : (nt <= 256 ? 128u : (nt <= 512 ? 256u : 512u));
 }
 
 template <int NT, int MODE>
@@ -151,12 +153,11 @@ struct TcUnit {
         if (threadIdx.x < 32) tmem_free(*reinterpret_cast<volatile uint32_t *>(area + kTcTmem), COLS);
     }
 
-    // v = DFT_16 v for the thread's group (forward), on the tensor cores. `a_smem` is the
-    // shared-memory address of the A rows (NT * 128 bytes, free to overwrite); `phase` the
-    // parity of this use of the group's mbarrier. The caller synchronises the CTA before
-    // (every read of the aliased buffer done) and after (every group's MMA done).
+    // v = DFT_16 v for the thread's group (forward), on the tensor cores; `phase` is the
+    // parity of this use of the group's mbarrier. Touches no shared memory but the DFT
+    // matrices and the mbarrier, so the caller needs no barrier around it.
     __device__ __forceinline__ static void dft16(const PassParams &p, float2 (&v)[16], unsigned char *area,
-                                                 uint32_t a_smem, uint32_t phase) {
+                                                 uint32_t phase) {
         constexpr bool bf = BF, split = SPLIT;
         const int tid = threadIdx.x, wg = tid >> 7, m = tid & 127;
         if constexpr (!bf) {
@@ -166,52 +167,41 @@ struct TcUnit {
                 v[t].y *= 0.25f;
             }
         }
-        const uint32_t aw = a_smem + wg * kTcAGroupBytes;
-        const uint32_t row = aw + (m >> 3) * kTcASbo + (m & 7) * 16;
-        if constexpr (split) {
-            uint32_t hr[8], hi_[8], lr[8], li[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                hr[j] = tc_split2(v[2 * j].x, v[2 * j + 1].x, bf, &lr[j]);
-                hi_[j] = tc_split2(v[2 * j].y, v[2 * j + 1].y, bf, &li[j]);
-            }
-            st_shared_v4(row + 0 * 128, hr[0], hr[1], hr[2], hr[3]);
-            st_shared_v4(row + 1 * 128, hr[4], hr[5], hr[6], hr[7]);
-            st_shared_v4(row + 2 * 128, hi_[0], hi_[1], hi_[2], hi_[3]);
-            st_shared_v4(row + 3 * 128, hi_[4], hi_[5], hi_[6], hi_[7]);
-            st_shared_v4(row + 4 * 128, lr[0], lr[1], lr[2], lr[3]);
-            st_shared_v4(row + 5 * 128, lr[4], lr[5], lr[6], lr[7]);
-            st_shared_v4(row + 6 * 128, li[0], li[1], li[2], li[3]);
-            st_shared_v4(row + 7 * 128, li[4], li[5], li[6], li[7]);
-        } else {
-            uint32_t hr[8], hi_[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                hr[j] = tc_pack2(v[2 * j].x, v[2 * j + 1].x, bf);
-                hi_[j] = tc_pack2(v[2 * j].y, v[2 * j + 1].y, bf);
-            }
-            st_shared_v4(row + 0 * 128, hr[0], hr[1], hr[2], hr[3]);
-            st_shared_v4(row + 1 * 128, hr[4], hr[5], hr[6], hr[7]);
-            st_shared_v4(row + 2 * 128, hi_[0], hi_[1], hi_[2], hi_[3]);
-            st_shared_v4(row + 3 * 128, hi_[4], hi_[5], hi_[6], hi_[7]);
-        }
-        fence_proxy_async_smem();  // the rows are read by the tensor cores
-        named_bar(1 + wg, 128);
-        uint64_t *bar = reinterpret_cast<uint64_t *>(area + kTcBars) + wg;
         const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(area + kTcTmem);
+        const uint32_t gcol = tmem + kTcGroupCols * wg;  // this group's columns, lane 0
+        const uint32_t lanes = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;  // this warp's lanes
+        if constexpr (split) {
+            uint32_t r[32];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                r[j] = tc_split2(v[2 * j].x, v[2 * j + 1].x, bf, &r[16 + j]);
+                r[8 + j] = tc_split2(v[2 * j].y, v[2 * j + 1].y, bf, &r[24 + j]);
+            }
+            tmem_st32(gcol + lanes + kTcACol, r);
+        } else {
+            uint32_t r[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                r[j] = tc_pack2(v[2 * j].x, v[2 * j + 1].x, bf);
+                r[8 + j] = tc_pack2(v[2 * j].y, v[2 * j + 1].y, bf);
+            }
+            tmem_st16(gcol + lanes + kTcACol, r);
+        }
+        tc_fence_before();
+        named_bar(1 + wg, 128);  // every row of the group's A is in tensor memory
+        uint64_t *bar = reinterpret_cast<uint64_t *>(area + kTcBars) + wg;
         if (m == 0) {
             tc_fence_after();
-            const uint32_t d = tmem + 32 * wg;  // columns of this group's 128 x 32 FP32 tile
             const uint32_t idesc = umma_idesc_f16(bf, 128, 32);
-            const uint32_t bhi = smem_u32(area), blo = bhi + kTcBLo;
-            // K = 16 steps: (A chunks, B chunks) = (re, re-rows of B), (im, im-rows of B)
-            umma_f16(d, umma_desc(aw, 128, kTcASbo), umma_desc(bhi, 128, 512), idesc, 0);
-            umma_f16(d, umma_desc(aw + 256, 128, kTcASbo), umma_desc(bhi + 256, 128, 512), idesc, 1);
+            const uint32_t bhi = smem_u32(area), blo = bhi + kTcBLo, a = gcol + kTcACol;
+            // K = 16 steps: (A columns, B chunks) = (re, re-rows of B), (im, im-rows of B)
+            umma_f16_ta(gcol, a, umma_desc(bhi, 128, 512), idesc, 0);
+            umma_f16_ta(gcol, a + 8, umma_desc(bhi + 256, 128, 512), idesc, 1);
             if constexpr (split) {
-                umma_f16(d, umma_desc(aw + 512, 128, kTcASbo), umma_desc(bhi, 128, 512), idesc, 1);        // lo.hi
-                umma_f16(d, umma_desc(aw + 768, 128, kTcASbo), umma_desc(bhi + 256, 128, 512), idesc, 1);
-                umma_f16(d, umma_desc(aw, 128, kTcASbo), umma_desc(blo, 128, 512), idesc, 1);              // hi.lo
-                umma_f16(d, umma_desc(aw + 256, 128, kTcASbo), umma_desc(blo + 256, 128, 512), idesc, 1);
+                umma_f16_ta(gcol, a + 16, umma_desc(bhi, 128, 512), idesc, 1);  // lo.hi
+                umma_f16_ta(gcol, a + 24, umma_desc(bhi + 256, 128, 512), idesc, 1);
+                umma_f16_ta(gcol, a, umma_desc(blo, 128, 512), idesc, 1);  // hi.lo
+                umma_f16_ta(gcol, a + 8, umma_desc(blo + 256, 128, 512), idesc, 1);
             }
             umma_commit(bar);
         }
@@ -220,7 +210,7 @@ struct TcUnit {
         tc_fence_after();
         __syncwarp();  // tcgen05.ld is warp-collective
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 32 * wg, r);
+        tmem_ld32(gcol + lanes, r);
 #pragma unroll
         for (int t = 0; t < 16; ++t) v[t] = make_float2(__uint_as_float(r[t]), __uint_as_float(r[16 + t]));
         tc_fence_before();
