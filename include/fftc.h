@@ -46,7 +46,8 @@ typedef enum { FFTC_FORWARD = -1, FFTC_INVERSE = +1 } fftc_direction;
 /* Arithmetic of the radix stages.
  * FP32:           every stage in float32 on CUDA cores.
  * *_TC:           radix-16 stages as dense 16x16 complex DFT-matrix products on the
- *                 tensor cores with FP16 or BF16 operands and FP32 accumulation.
+ *                 tensor cores with FP16 or BF16 operands and FP32 accumulation (for
+ *                 n = 2^13 and 2^14 radix-32 stages as 32x32 products, one stage fewer).
  * *_TC_SPLIT:     as *_TC, but each operand is split into hi + lo parts and the three
  *                 products hi*hi + hi*lo + lo*hi are accumulated, recovering most of
  *                 the FP32 accuracy.
@@ -86,7 +87,7 @@ typedef enum {
  * Precomputes the twiddle diagonals D (Eq. 1; Table 1 "Mul") in FP64 with exact
  * integer angle reduction and rounds them once to the working precision.
  * Returns NULL on error; fftc_get_last_error() then tells why.
- * Tensor-core precisions require a power of two n >= 16. FFTC_FP64 takes any n the
+ * Tensor-core precisions require a power of two 2^7 <= n <= 2^16. FFTC_FP64 takes any n the
  * FP32 path takes (one pass up to 4096, two above, both factors at most 4096); its
  * buffers hold complex128.
  */

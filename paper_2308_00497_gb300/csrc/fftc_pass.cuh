@@ -67,19 +67,20 @@ struct Pass {
     static constexpr int C_LINES = C, LIN_LAYOUT = LIN, KIND_ID = KIND;
     static constexpr int LINE_WORDS = L + (L >> LOGE);
     static constexpr int PITCH = pass_pitch(LINE_WORDS, C);
-    // TC: radix-16 stages on the tensor cores (fftc_tc.cuh); the tensor-core area sits in
-    // front of the data in dynamic shared memory, and a stage's A rows alias the tile buffer
-    static constexpr int TC_BYTES = TC ? kTcAreaBytes : 0;
+    // TC: the radix-E stages (E = 16 or 32) on the tensor cores (fftc_tc.cuh); the
+    // tensor-core area (DFT matrices, mbarriers) sits in front of the data in dynamic shared
+    // memory; a shorter last stage runs on the CUDA cores
+    static constexpr int TC_BYTES = TC ? tc_area_bytes(E) : 0;
     static constexpr int DATA_BYTES = (S > 1) ? C * PITCH * (int)sizeof(float2) : 0;
     static constexpr int SMEM = TC ? TC_BYTES + DATA_BYTES + 128 : DATA_BYTES;
-    static_assert(!TC || (LOGE == 4 && NT % 128 == 0 && !IDX), "tensor-core passes: 16 elements per thread");
-    static_assert(!TC || DATA_BYTES >= NT * 128, "the A rows must fit in the tile buffer");
+    static_assert(!TC || ((LOGE == 4 || LOGE == 5) && NT % 128 == 0 && !IDX),
+                  "tensor-core passes: 16 or 32 elements per thread");
     __host__ __device__ static constexpr int tc_count(int upto) {
         int c = 0;
-        for (int i = 0; i < upto; ++i) c += (Sc::lr(i) == 4) ? 1 : 0;
+        for (int i = 0; i < upto; ++i) c += (Sc::lr(i) == LOGE) ? 1 : 0;
         return c;
     }
-    static constexpr int NTC = TC ? tc_count(S) : 0;  // radix-16 stages per tile
+    static constexpr int NTC = TC ? tc_count(S) : 0;  // tensor-core stages per tile
     __host__ __device__ static constexpr float tc_out_scale() {
         float f = 1.f;
         for (int i = 0; i < NTC; ++i) f *= 4.f;
@@ -103,7 +104,7 @@ struct Pass {
     static constexpr bool WARP_SYNC = all_tau() && TPL <= 32 && (32 % TPL) == 0;
     // registers per thread the launch bounds aim at: E = 32 needs ~128; E = 16 fits 80, or 64
     // for 512-thread CTAs so that two of them share an SM
-    static constexpr int REG_TARGET = TC ? 64 : (E >= 32 ? 128 : (E >= 16 ? (NT >= 512 ? 64 : 80) : 64));
+    static constexpr int REG_TARGET = TC ? (E >= 32 ? 128 : 64) : (E >= 32 ? 128 : (E >= 16 ? (NT >= 512 ? 64 : 80) : 64));
     static constexpr int MINB = (65536 / (NT * REG_TARGET)) > 0 ? (65536 / (NT * REG_TARGET)) : 1;
     // element strides: compile-time unless LOGX == 0 for a four-step kind
     static constexpr int ES_IN_CT = COLS_LIKE ? (LOGX ? (1 << LOGX) : 0) : 1;
@@ -263,7 +264,7 @@ struct Pass {
                                                  const H &hook = H(), uint32_t tk = 0) {
         constexpr int LR = Sc::lr(s), R = 1 << LR, LNS = Sc::lns(s), NS = 1 << LNS;
         constexpr bool TF = tau_fast(s);
-        constexpr bool TCS = TC && LR == 4;  // this stage's butterfly runs on the tensor cores
+        constexpr bool TCS = TC && LR == LOGE;  // this stage's butterfly runs on the tensor cores
         const int c = TF ? tid / TPL : tid % C;
         const int tau = TF ? tid % TPL : tid / C;
         const int64_t g = g0 + c;
@@ -302,7 +303,7 @@ struct Pass {
         if constexpr (TCS) {
             // the i-th tensor-core stage of this CTA's k-th tile uses mbarrier phase (k NTC + i) mod 2
             const uint32_t phase = (tk * NTC + tc_count(s)) & 1u;
-            TcUnit<NT, TCM>::dft16(p, v, dyn_smem_base128(), phase);
+            TcUnit<NT, TCM, E>::dft(p, v, dyn_smem_base128(), phase);
         } else {
 #pragma unroll
             for (int q = 0; q < E / R; ++q) dft<R>(v + q * R);
@@ -361,7 +362,7 @@ struct Pass {
             // persistent: the set-up (DFT matrices, mbarriers, TMEM columns) is paid once per CTA
             unsigned char *area = dyn_smem_base128();
             float2 *sm = reinterpret_cast<float2 *>(area + TC_BYTES);
-            TcUnit<NT, TCM>::setup(p, area);
+            TcUnit<NT, TCM, E>::setup(p, area);
             const int64_t ntiles = (p.total_lines + C - 1) / C;
             uint32_t tk = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tk) {
@@ -370,7 +371,7 @@ struct Pass {
                 stage<0>(p, sm, v, threadIdx.x, tile * C, NoHook(), tk);
                 __syncthreads();  // the tile's last shared reads precede the next tile's A rows
             }
-            TcUnit<NT, TCM>::teardown(area);
+            TcUnit<NT, TCM, E>::teardown(area);
         } else {
             stage<0>(p, sm_dyn, v, threadIdx.x, (int64_t)blockIdx.x * C);
         }
@@ -439,7 +440,7 @@ int resident_ctas() {
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;
         const int per_sm = resident_per_sm((const void *)k_pass<LOGL, LOGE, C, KIND, LIN, LOUT, LOGX, TCM>, P::NT,
-                                           P::SMEM, TCM ? (int)tc_tmem_cols(P::NT) : 0);
+                                           P::SMEM, TCM ? (int)tc_tmem_cols(P::NT, P::E) : 0);
         r = per_sm * sms;
     }
     return r;

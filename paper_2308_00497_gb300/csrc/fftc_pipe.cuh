@@ -121,7 +121,7 @@ struct PipeTile {
             for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
             fence_mbar_init();
         }
-        if constexpr (P::NTC > 0) TcUnit<NT, P::TCM_ID>::setup(p, area);  // ends with a CTA barrier
+        if constexpr (P::NTC > 0) TcUnit<NT, P::TCM_ID, P::E>::setup(p, area);  // ends with a CTA barrier
         __syncthreads();
         if (threadIdx.x == 0)
             for (int b = 0; b < NBUF; ++b) {
@@ -154,7 +154,7 @@ struct PipeTile {
                 if (next < ntiles) refill(a, next, buf, &bars[b]);
             }
         }
-        if constexpr (P::NTC > 0) TcUnit<NT, P::TCM_ID>::teardown(area);
+        if constexpr (P::NTC > 0) TcUnit<NT, P::TCM_ID, P::E>::teardown(area);
     }
 };
 
@@ -180,7 +180,7 @@ struct PipeLauncher {
         int sms = 0, dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         const int per_sm = resident_per_sm((const void *)k_pipe<P, NBUF, EARLY>, PT::NT, PT::SMEM,
-                                           P::NTC > 0 ? (int)tc_tmem_cols(PT::NT) : 0);
+                                           P::NTC > 0 ? (int)tc_tmem_cols(PT::NT, P::E) : 0);
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid_cache() = (per_sm > 0 ? per_sm : 1) * sms;
         return cudaSuccess;

@@ -112,6 +112,12 @@ static const PipeRowsDefault *pipe_rows_default(int logn) {
     return nullptr;
 }
 
+// Elements per thread (log2) of the tensor-core single pass: 5 (radix-32 stages) at 2^13
+// and 2^14, where it measured 12-16 % faster than radix-16 stages (one stage and one
+// exchange fewer), else 4 (at 2^12 the radix-16 tiles keep three CTAs per SM and win);
+// FFTC_TUNE_TC_E overrides it.
+static int tc_rows_loge(int logn) { return (logn == 13 || logn == 14) ? 5 : 4; }
+
 // bounded waits: FFTC_SPIN_LIMIT sets the poll limit of the pipelined kernels, and
 // FFTC_TEST_UNREACHABLE_WAIT (a test hook) makes them issue no copy so every wait runs out
 static void set_wait_hooks(PassParams &b) {
@@ -264,16 +270,25 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         p->npasses = 1;
         pp.kind = KIND_ROWS;
         pp.logl = p->logn;
-        if (tc) {  // 16 elements per thread; 256-thread tiles up to 2^12, one line per tile above
-            pp.loge = 4;
-            pp.lines = p->logn >= 12 ? 1 : (4096 >> p->logn);
+        if (tc) {
+            // radix-32 stages on 32-element threads (one line per tile, one landing buffer)
+            // where tc_rows_loge says so, else radix-16 stages on 16-element threads
+            // (256-thread tiles up to 2^12, one line per tile above)
+            pp.loge = env_int("FFTC_TUNE_TC_E", tc_rows_loge(p->logn));
+            pp.lines = (pp.loge == 5 || p->logn >= 12) ? 1 : (4096 >> p->logn);
         } else if (!choose_rows(p->logn, lay, &pp.loge, &pp.lines)) {
             return FFTC_ERR_UNSUPPORTED_SIZE;
         }
         pp.lin = pp.lout = lay;
         pp.k = find_kernel(KIND_ROWS, pp.logl, pp.loge, pp.lines, lay, lay, prec);
-        if (tc && !pp.k)  // n >= 2^9: bulk-copy fed (two landing buffers up to 2^12, one above)
-            pp.k = find_kernel(KIND_ROWS, pp.logl, 4, pp.lines, lay, lay, prec, 0, p->logn <= 12 ? 6 : 5);
+        if (tc && !pp.k && pp.loge == 5)  // n = 2^12 .. 2^14: bulk-copy fed, one landing buffer
+            pp.k = find_kernel(KIND_ROWS, pp.logl, 5, 1, lay, lay, prec, 0, 5);
+        if (tc && !pp.k) {  // n >= 2^9: bulk-copy fed (two landing buffers up to 2^12, one above)
+            pp.loge = 4;
+            pp.lines = p->logn >= 12 ? 1 : (4096 >> p->logn);
+            pp.k = find_kernel(KIND_ROWS, pp.logl, 4, pp.lines, lay, lay, prec);
+            if (!pp.k) pp.k = find_kernel(KIND_ROWS, pp.logl, 4, pp.lines, lay, lay, prec, 0, p->logn <= 12 ? 6 : 5);
+        }
         // pipelined persistent kernel where it measured faster (n = 2^9 .. 2^14)
         const PipeRowsDefault *pd = pipe_rows_default(p->logn);
         if (!tc && env_int("FFTC_PIPE", pd ? 1 : 0)) {

@@ -1,9 +1,11 @@
-"""Tensor-core radix-16 precisions against the FP64 oracle.
+"""Tensor-core precisions (radix-16 and radix-32 stages) against the FP64 oracle.
 
 The paper evaluates FP64 only, so these bounds are derived here from the unit roundoff u
-of each operand format and frozen: a radix-16 stage rounds its inputs and W16 once each,
-so the relative L2 error after s tensor-core stages stays below 2 (s + 1) u, plus the
-FP32 bound of the rest of the path (twiddles, leftover radix, accumulation):
+of each operand format and frozen: a tensor-core stage rounds its inputs and the DFT
+matrix once each, so the relative L2 error after s tensor-core stages stays below
+2 (s + 1) u, plus the FP32 bound of the rest of the path (twiddles, leftover radix,
+accumulation). s is taken as the radix-16 stage count log2(n) // 4, which is at least the
+radix-32 stage count log2(n) // 5 of the 32-element kernels:
 
     FP16 plain  u = 2^-11     BF16 plain  u = 2^-8
     FP16 split  u = 2^-22     BF16 split  u = 2^-16   (hi + lo carry twice the bits)
@@ -150,3 +152,29 @@ def test_tuned_tc_plan(mode, e):
     rows = np.array([0, B - 1])
     ref = oracle.fft(x[rows].astype(np.complex128))
     assert rel_l2_rows(from_device(a, "interleaved")[rows], ref).max() <= bound(mode, n)
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("mode", list(U))
+@pytest.mark.parametrize("e", [12, 13, 14])
+@pytest.mark.parametrize("loge", [4, 5])
+def test_tc_radix16_and_radix32_kernels(monkeypatch, layout, inverse, mode, e, loge):
+    """Both tensor-core single passes of n = 2^12 .. 2^14, whichever the default picks:
+    16 elements per thread (radix-16 stages as 32 x 32 real DFT-matrix products) and 32
+    (radix-32 stages as 64 x 64 products, the remaining radix on the CUDA cores), in both
+    layouts and directions, with a ragged persistent schedule (batch not a multiple of the
+    grid)."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_TUNE_TC_E", str(loge))
+    n = 1 << e
+    B = 7
+    x = si.gaussian_complex(B, n, seed=800 + e)
+    p = fc.Plan(n, B, layout, inverse, mode)
+    r = 1 << loge
+    assert p.info()[1][:2] == [r, r], p.info()
+    y = p.execute(to_device(x, layout))
+    torch.cuda.synchronize()
+    ref = oracle.fft(x.astype(np.complex128), inverse=inverse)
+    err = rel_l2_rows(from_device(y, layout), ref).max()
+    assert err <= bound(mode, n), (mode, n, float(err))
