@@ -208,6 +208,14 @@ fftc_plan fftc_plan_create_nd(int rank, const int64_t *dims, int64_t batch, fftc
  * one persistent-kernel launch, replayed from a CUDA graph captured at the first
  * execute on a given (in, out, stream). n, direction and offset are host arrays,
  * copied into the plan. Only FFTC_FP32 is supported here.
+ * The plan is autotuned when it is created (the runtime planning the paper leaves to
+ * future work, Section 6): for every length class, each compiled factorisation (one pass,
+ * or Eq. 1 once at the memory level, n = M K, for every split with kernels) and tile shape
+ * (elements per thread: the default, half of it, or 16 with 4096-element tiles, which
+ * fixes the radix of the stages and the lines per tile) is timed inside the persistent
+ * kernel on scratch buffers allocated and freed in this call, and the fastest is kept;
+ * choices are cached per device for the process and, with FFTC_TUNE_CACHE naming a file,
+ * across processes. FFTC_TUNE=0 takes the default table instead.
  */
 fftc_plan fftc_plan_create_uneven(int64_t count, const int64_t *n, const int8_t *direction,
                                   const int64_t *offset, fftc_layout layout,

@@ -33,9 +33,12 @@ namespace fftc {
 
 // (id, LOGL, LOGE, C, KIND, IDX, LOGX): every branch has C * 2^(LOGL - LOGE) = 256
 // threads; the four-step branches carry their element stride 2^LOGX at compile time
-// (one pair per split n = M K of the classes 2^13 .. 2^16). Branches 19.. are the "half"
+// (one pair per split n = M K of the classes 2^13 .. 2^16). Branches 19..34 are the "half"
 // variants: half the elements per thread, so twice the threads per line, half the lines
-// per tile and one more radix stage (the autotuner's tile-shape / stages-per-pass choice).
+// per tile and one more radix stage; branches 35.. the "wide" four-step variants: 16
+// elements per thread whatever the line length, so short lines (64, 128) come in tiles of
+// 4096 elements (64 or 32 lines) instead of 16 lines (the autotuner's tile-shape /
+// stages-per-pass choice).
 #define FFTC_UNEVEN_BRANCHES(X)                \
     X(0, 6, 4, 64, KIND_ROWS, true, 0)         \
     X(1, 7, 4, 32, KIND_ROWS, true, 0)         \
@@ -71,7 +74,19 @@ namespace fftc {
     X(31, 7, 2, 8, KIND_ROWST, false, 7)       \
     X(32, 7, 2, 8, KIND_ROWST, false, 8)       \
     X(33, 8, 3, 8, KIND_ROWST, false, 7)       \
-    X(34, 8, 3, 8, KIND_ROWST, false, 8)
+    X(34, 8, 3, 8, KIND_ROWST, false, 8)       \
+    X(35, 6, 4, 64, KIND_COLS, false, 7)       \
+    X(36, 6, 4, 64, KIND_COLS, false, 8)       \
+    X(37, 7, 4, 32, KIND_COLS, false, 6)       \
+    X(38, 7, 4, 32, KIND_COLS, false, 7)       \
+    X(39, 7, 4, 32, KIND_COLS, false, 8)       \
+    X(40, 8, 4, 16, KIND_COLS, false, 6)       \
+    X(41, 6, 4, 64, KIND_ROWST, false, 7)      \
+    X(42, 6, 4, 64, KIND_ROWST, false, 8)      \
+    X(43, 7, 4, 32, KIND_ROWST, false, 6)      \
+    X(44, 7, 4, 32, KIND_ROWST, false, 7)      \
+    X(45, 7, 4, 32, KIND_ROWST, false, 8)      \
+    X(46, 8, 4, 16, KIND_ROWST, false, 6)
 
 #define FFTC_BRANCH_TYPE(ID, LOGL, LOGE, C, KIND, IDX, LOGX) \
     Pass<LOGL, LOGE, C, KIND, LAYOUT_IL, LAYOUT_IL, IDX, LOGX>
@@ -245,8 +260,9 @@ static int find_branch(int kind, int logl, int loge, int lines, int logx = 0) {
 }
 
 // Configuration of one length class: single pass (logm = 0) or four-step (logm > 0), with
-// the default elements per thread (ev = 0) or half of them (ev = 1: twice the threads per
-// line, half the lines per tile, one more radix stage). Passed around as one int code.
+// the default elements per thread (ev = 0), half of them (ev = 1: twice the threads per
+// line, half the lines per tile, one more radix stage) or, four-step only, 16 elements per
+// thread on every line length (ev = 2: 4096-element tiles). Passed around as one int code.
 struct ClassCfg {
     int logm = 0;  // four-step split n = 2^logm * 2^(logn - logm); 0 = single pass
     int ev = 0;
@@ -266,11 +282,16 @@ static int env_int(const char *name, int dflt) {
 
 
 static int rows_branch(int logn, int ev) {
+    if (ev > 1) return -1;
     const int loge = 4 - ev;
     return logn > loge ? find_branch(KIND_ROWS, logn, loge, 256 >> (logn - loge)) : -1;
 }
-static int cols_branch(int logm, int logk, int ev) { return find_branch(KIND_COLS, logm, logm - 4 - ev, 16 >> ev, logk); }
+static int cols_branch(int logm, int logk, int ev) {
+    if (ev == 2) return find_branch(KIND_COLS, logm, 4, 256 >> (logm - 4), logk);
+    return find_branch(KIND_COLS, logm, logm - 4 - ev, 16 >> ev, logk);
+}
 static int rowst_branch(int logk, int logm, int ev) {
+    if (ev == 2) return find_branch(KIND_ROWST, logk, 4, 256 >> (logk - 4), logm);
     return find_branch(KIND_ROWST, logk, logk - 4 - ev, 16 >> ev, logm);
 }
 
@@ -616,10 +637,13 @@ static std::vector<int> candidates(int logn) {
     for (int logm = 0; logm <= 8; ++logm) {
         if (logm > 0 && logm < 6) continue;
         if (logm > 0 && (logn - logm < 6 || logn - logm > 8)) continue;
-        for (int ev = 0; ev <= 1; ++ev) {
+        for (int ev = 0; ev <= 2; ++ev) {
             ClassCfg cc;
             cc.logm = logm;
             cc.ev = ev;
+            if (ev == 2 && logm > 0 && cols_branch(logm, logn - logm, 2) == cols_branch(logm, logn - logm, 0) &&
+                rowst_branch(logn - logm, logm, 2) == rowst_branch(logn - logm, logm, 0))
+                continue;  // the same branches as the default variant
             if (class_supported(logn, cc)) c.push_back(cc.code());
         }
     }
@@ -685,7 +709,8 @@ static void read_tune_file(const std::string &dev) {
     fclose(f);
 }
 
-// one line per choice: "uneven <device name>|<log2 n> <log2 M (0: one pass)> <half-E variant>"
+// one line per choice: "uneven <device name>|<log2 n> <log2 M (0: one pass)> <tile variant>"
+// (0: the default elements per thread, 1: half of them, 2: 16 on every line length)
 static void append_tune_file(const std::string &dev, int logn, int code) {
     const char *path = getenv("FFTC_TUNE_CACHE");
     if (!path || !*path) return;

@@ -105,6 +105,34 @@ def test_bounded_wait_reports_timeout(monkeypatch):
     assert torch.isfinite(y.view(torch.float32)).all()
 
 
+# every compiled four-step configuration of the classes 2^13 .. 2^16: (log2 n, log2 M, variant)
+# with variant 0 = 2^(L - 4) elements per thread, 16 lines a tile; 1 = half of them; 2 = 16
+# elements per thread on every line length (4096-element tiles)
+FOUR_STEP_CONFIGS = [(13, 6, 0), (13, 7, 0), (14, 7, 0), (15, 7, 0), (15, 8, 0), (16, 8, 0),
+                     (14, 7, 1), (15, 7, 1), (15, 8, 1), (16, 8, 1),
+                     (13, 6, 2), (13, 7, 2), (14, 6, 2), (14, 7, 2), (14, 8, 2), (15, 7, 2), (15, 8, 2)]
+
+
+@pytest.mark.parametrize("logn,logm,ev", FOUR_STEP_CONFIGS)
+def test_every_four_step_branch(monkeypatch, logn, logm, ev):
+    """Each four-step split and tile shape the autotuner may pick for a length class, forced
+    through its override, on rows of both directions beside a single-pass class; every row
+    against the oracle."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv(f"FFTC_UNEVEN_LOGM_{logn}", str(logm))
+    monkeypatch.setenv(f"FFTC_UNEVEN_EV_{logn}", str(ev))
+    n = np.array([1 << logn] * 5 + [256] * 3, dtype=np.int64)
+    d = np.array([-1, 1, -1, 1, 1, -1, 1, -1], dtype=np.int8)
+    o = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    total = int(o[-1] + n[-1])
+    x = si.uniform_complex(1, total, seed=40 + logn + 3 * logm + ev).reshape(total)
+    p = fc.UnevenPlan(n, d, o)
+    y = p.execute(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    p.check()
+    _check_rows(x, y.cpu().numpy(), n, d, o, range(n.size))
+
+
 def test_uneven_rejects_bad_descriptors():
     import paper_2308_00497_gb300 as fc
     from paper_2308_00497_gb300 import _native as nat
@@ -154,7 +182,7 @@ def test_tune_cache_file_round_trip(tmp_path):
     still within tolerance of the oracle)."""
     cache = tmp_path / "tune.txt"
     y1 = _cache_run(tmp_path, cache, "first")
-    # "uneven <device name>|<log2 n> <log2 M, 0 for one pass> <half-elements-per-thread variant>"
+    # "uneven <device name>|<log2 n> <log2 M, 0 for one pass> <tile variant: 0, 1 half, 2 wide>"
     lines = [ln.split() for ln in cache.read_text().splitlines() if ln.startswith("uneven ")]
     chosen = {int(t[-3].split("|")[-1]): (int(t[-2]), int(t[-1])) for t in lines}
     assert {13, 15} <= set(chosen)
