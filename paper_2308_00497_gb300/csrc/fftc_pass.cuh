@@ -57,8 +57,8 @@ __device__ __forceinline__ unsigned char *dyn_smem_base128() {
 
 template <int LOGL, int LOGE, int C, int KIND, int LIN, int LOUT, bool IDX = false, int LOGX = 0, int TCM = 0>
 struct Pass {
-    // TCM: 0 = every stage on the CUDA cores; 1..4 = the radix-16 stages on the tensor cores
-    // in that precision mode (TcMode)
+    // TCM: 0 = every stage on the CUDA cores; 1..4 = the radix-E stages (E = 16 or 32) on the
+    // tensor cores in that precision mode (TcMode)
     static constexpr bool TC = TCM != 0;
     static constexpr int TCM_ID = TCM;
     using Sc = Sched<LOGL, LOGE>;

@@ -52,9 +52,6 @@ __host__ __device__ constexpr bool tc_is_split(int mode) { return mode == TC_FP1
 //   [2 BB + 64]     TMEM base address written by tcgen05.alloc
 __host__ __device__ constexpr int tc_b_bytes(int r) { return 2 * r * 2 * r * 2; }
 __host__ __device__ constexpr int tc_area_bytes(int r) { return 2 * tc_b_bytes(r) + 128; }
-// Tensor memory of a 128-thread group g: 4R columns from 4R g, the FP32 D tile (2R columns:
-// R real then R imaginary outputs) then the A rows (FP16/BF16 pairs, lower K in the low half:
-// hi re, hi im, lo re, lo im, R / 2 columns each)
 
 __device__ __forceinline__ uint32_t tc_pack2(float a, float b, bool bf) {
     if (bf) {
@@ -127,7 +124,10 @@ struct TcUnit {
     static constexpr int BB = tc_b_bytes(R);            // one B matrix
     static constexpr int BSBO = (N2 / 8) * 128;         // bytes between 8-row groups of B
     static constexpr int BARS = 2 * BB, TMEM_SLOT = 2 * BB + 64;
-    static constexpr uint32_t GCOLS = 4 * R, ACOL = N2;  // TMEM columns per group; A after D
+    // Tensor memory of 128-thread group g: GCOLS columns from GCOLS g, the FP32 D tile (2R
+    // columns: R real then R imaginary outputs) then the A rows from column ACOL (FP16/BF16
+    // pairs, the lower K in the low half: hi re, hi im, lo re, lo im, R / 2 columns each)
+    static constexpr uint32_t GCOLS = 4 * R, ACOL = N2;
     static constexpr uint32_t COLS = tc_tmem_cols(NT, R);
 
     // every thread: DFT matrices into shared memory, mbarriers, TMEM columns
