@@ -451,7 +451,7 @@ def test_tune_cache_carries_plan_choices(tmp_path):
     (15, 7, 4, 32, 0), (16, 8, 4, 32, 0), (17, 8, 4, 32, 0), (16, 8, 5, 32, 0), (17, 8, 5, 32, 0),
     (15, 7, 4, 32, 5), (16, 8, 4, 32, 5), (17, 8, 4, 32, 5),
     (20, 9, 4, 16, 5), (20, 9, 4, 32, 5), (20, 10, 4, 16, 5), (20, 10, 5, 8, 5),
-    (19, 9, 5, 32, 0), (20, 9, 5, 32, 0), (19, 9, 4, 32, 5),
+    (19, 9, 5, 32, 0), (20, 9, 5, 32, 0), (19, 9, 4, 32, 5), (20, 9, 4, 16, 0), (20, 9, 5, 16, 0),
 ])
 @pytest.mark.parametrize("layout", ["interleaved", "split"])
 def test_pass1_band_variants(monkeypatch, e, logm, loge, lines, p1, layout):
@@ -476,4 +476,26 @@ def test_pass1_band_variants(monkeypatch, e, logm, loge, lines, p1, layout):
     p.check()
     rows = np.array([0, B // 2, B - 1])
     ref = oracle.fft(x[rows].astype(np.complex128), inverse=e % 2 == 0)
+    assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_2p20_pass2_bulk_copy_compile_time_stride(monkeypatch, layout, inverse):
+    """n = 2^20 split as 2^9 x 2^11 with pass 2 fed by one bulk copy per tile of 8 rows of
+    2048 points and its transposed store at the compile-time stride 2^9, against the oracle
+    on sampled rows."""
+    import paper_2308_00497_gb300 as fc
+    for k, v in (("FFTC_TUNE_FOURSTEP_LOGM", 9), ("FFTC_TUNE_ROWST_E", 5), ("FFTC_TUNE_ROWST_C", 8),
+                 ("FFTC_PIPE4", 2), ("FFTC_TUNE_P2_PIPE", 5)):
+        monkeypatch.setenv(k, str(v))
+    n, B = 1 << 20, 5
+    x = si.uniform_complex(B, n, seed=91)
+    p = fc.Plan(n, B, layout, inverse)
+    assert p.split() == (512, 2048)
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    rows = np.array([0, B - 1])
+    ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
     assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
