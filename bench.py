@@ -458,12 +458,26 @@ def run_uneven(args, dev, reps: int) -> dict:
         for (xb, yb), p in zip(bufs, plans):
             p.execute(xb, yb)
     t_sep = _time_ms(per_class, reps)
+    # the same launches replayed from one CUDA graph (no host launch overhead between them)
+    t_graph = None
+    try:
+        per_class()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            per_class()
+        t_graph = _time_ms(g.replay, reps)
+        del g
+    except RuntimeError:
+        t_graph = None
     res = {"workload": "4096 rows, n=2^6..2^16 log-uniform, mixed fwd/inv, interleaved, one persistent "
                        "launch from a CUDA graph", "elements": int(total), "ms": round(t_uneven, 4),
            "gflops": round(fl / (t_uneven * 1e-3) / 1e9, 1),
            "hbm_frac_strict": round(16.0 * total / (t_uneven * 1e-3) / 1e9 / peaks()[0], 4),
            "separate_launches_ms": round(t_sep, 4), "separate_launches": len(plans),
-           "speedup_vs_separate": round(t_sep / t_uneven, 3)}
+           "speedup_vs_separate": round(t_sep / t_uneven, 3),
+           "separate_launches_graph_ms": round(t_graph, 4) if t_graph else None,
+           "speedup_vs_separate_graph": round(t_graph / t_uneven, 3) if t_graph else None}
     del bufs, plans, x, y
     return res
 

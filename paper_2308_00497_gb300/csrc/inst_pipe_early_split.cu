@@ -15,6 +15,8 @@ extern const KernelEntry kPipeEarlySplitTable[] = {
     PRE(14, 5, 1, 1),     PRE(12, 5, 1, 1),
     PTE(8, 4, 16, 7, 2),  PTE(8, 4, 16, 8, 2),  PTE(9, 5, 8, 8, 2),   PTE(10, 5, 8, 8, 2),  PTE(10, 5, 8, 9, 2),
     PTE(10, 5, 8, 10, 2),
+    // 16-row tiles (16 consecutive outputs per plane and store) for n = 2^17 .. 2^19
+    PTE(9, 5, 16, 8, 1),  PTE(10, 5, 16, 8, 1), PTE(10, 5, 16, 9, 1),
     PCE(7, 4, 16, 8, 1),  PCE(8, 4, 16, 8, 1),  PCE(8, 4, 16, 9, 1),  PCE(8, 4, 32, 10, 1), PCE(9, 4, 16, 10, 1),
     // n = 2^20 as 2^9 x 2^11 and 2^10 x 2^10: 16 or 32 columns, 8 to 16 elements per thread
     PCE(9, 4, 16, 11, 1), PCE(9, 4, 32, 11, 1), PCE(10, 4, 16, 10, 1), PCE(10, 5, 8, 10, 1),

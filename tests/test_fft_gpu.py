@@ -499,3 +499,25 @@ def test_2p20_pass2_bulk_copy_compile_time_stride(monkeypatch, layout, inverse):
     rows = np.array([0, B - 1])
     ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
     assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("e,logm,logk", [(17, 8, 9), (18, 8, 10), (19, 9, 10)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_split_pass2_16_row_tiles(monkeypatch, e, logm, logk, inverse):
+    """Split-layout output through the bulk-copy fed pass 2 with 16-row tiles (16 consecutive
+    outputs per plane in each transposed store), against the oracle on sampled rows."""
+    import paper_2308_00497_gb300 as fc
+    for k, v in (("FFTC_TUNE_FOURSTEP_LOGM", logm), ("FFTC_TUNE_ROWST_E", 5), ("FFTC_TUNE_ROWST_C", 16),
+                 ("FFTC_PIPE4", 2), ("FFTC_TUNE_P2_PIPE", 5)):
+        monkeypatch.setenv(k, str(v))
+    n = 1 << e
+    B = max(3, (1 << 22) // n)
+    x = si.uniform_complex(B, n, seed=e + 300)
+    p = fc.Plan(n, B, "split", inverse)
+    assert p.split() == (1 << logm, 1 << logk)
+    y = from_device(p.execute(to_device(x, "split")), "split")
+    torch.cuda.synchronize()
+    p.check()
+    rows = np.array([0, B // 2, B - 1])
+    ref = oracle.fft(x[rows].astype(np.complex128), inverse=inverse)
+    assert rel_l2_rows(y[rows], ref).max() <= tol_fp32(n)
