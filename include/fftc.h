@@ -100,6 +100,10 @@ fftc_plan fftc_plan_create(int64_t n, int64_t batch, fftc_layout layout, fftc_di
  * (in place) is allowed; otherwise the buffers must not overlap. For an uneven plan
  * the buffers hold the rows back to back at the plan's offsets.
  * Returns FFTC_OK once the work is enqueued (kernel faults surface on the stream).
+ * Allocates and synchronises nothing (the plan owns every table and workspace), so a
+ * call on a stream under CUDA stream capture is recorded into the graph and replays on
+ * the buffers given at capture (1D, tensor-core, mixed-radix, FP64 and multidimensional
+ * plans). A plan must not run on two streams at once: its workspace is shared.
  */
 fftc_status fftc_execute(fftc_plan plan, const void *in, void *out, void *stream);
 
