@@ -83,7 +83,9 @@ typedef enum {
  * or (FFTC_FP32 only) any n = 2^a 3^b 5^c 7^d: Eq. 1 with mixed radices 16, 8, 4, 2,
  * 7, 5 and 3 (the mixed radix the paper names as missing, Sections 4 and 6), one
  * pass up to n = 8192 and two passes (n = M K) above. Powers of two take one pass up
- * to 2^14 and two above (Eq. 1 once at the memory level, factors up to 2^12).
+ * to 2^14, two above (Eq. 1 once at the memory level, factors up to 2^12) and three at
+ * 2^24 (Eq. 1 twice, n = 2^8 P Q, factors up to 2^8; the environment variable
+ * FFTC_THREE_PASS = 1 or 0 forces that form on or off for 2^21 and above).
  * Precomputes the twiddle diagonals D (Eq. 1; Table 1 "Mul") in FP64 with exact
  * integer angle reduction and rounds them once to the working precision.
  * Returns NULL on error; fftc_get_last_error() then tells why.
@@ -161,7 +163,8 @@ fftc_status fftc_plan_info(fftc_plan plan, int *passes, int *radices, int *n_rad
 /*
  * The split of a 1D plan into HBM passes: *m and *k with m * k = n, m the length of the
  * pass-1 column transforms and k of the pass-2 row transforms of the four-step form
- * (Eq. 1 applied once at the memory level, N = M K). A one-pass plan reports m = n, k = 1.
+ * (Eq. 1 applied once at the memory level, N = M K). A one-pass plan reports m = n, k = 1;
+ * a three-pass plan m = 2^8 and k = n / 2^8 (its two last passes split k once more).
  * Either pointer may be NULL. FFTC_ERR_INVALID_VALUE for uneven and multidimensional plans.
  */
 fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k);
@@ -185,7 +188,8 @@ fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k);
  * choices are also appended to it and read back by later processes (FFTW's "wisdom").
  * Synchronises the device; do not call it while the plan executes. Tensor-core plans choose
  * among the kernels of their own precision mode; uneven plans are tuned when they are
- * created (fftc_plan_create_uneven) and are returned unchanged. reps in [1, 1000].
+ * created (fftc_plan_create_uneven) and are returned unchanged, and so are three-pass
+ * plans. reps in [1, 1000].
  */
 fftc_status fftc_plan_tune(fftc_plan plan, int reps);
 

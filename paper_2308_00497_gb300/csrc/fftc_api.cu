@@ -284,7 +284,7 @@ fftc_status fftc_plan_split(fftc_plan plan, int64_t *m, int64_t *k) {
     if (plan->mixed) {
         mm = mixed_plan_split(plan);
         kk = plan->n / mm;
-    } else if (plan->npasses == 2 || plan->fs || plan->cluster) {
+    } else if (plan->npasses >= 2 || plan->fs || plan->cluster) {
         mm = int64_t(1) << plan->pass[0].logl;
         kk = plan->n / mm;
     }

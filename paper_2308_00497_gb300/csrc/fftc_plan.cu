@@ -112,6 +112,11 @@ static const PipeRowsDefault *pipe_rows_default(int logn) {
     return nullptr;
 }
 
+// smallest log2 n planned as three HBM passes by default: measured (n * batch = 2^26,
+// forward) against the two-pass form, 2^24 1.08x (interleaved) and 1.32x (split) faster,
+// 2^23 even, 2^21 and 2^22 0.62-0.76x (the middle pass runs once per transform)
+static constexpr int kThreePassMinLog = 24;
+
 // Elements per thread (log2) of the tensor-core single pass: 5 (radix-32 stages) at 2^13
 // and 2^14, where it measured 12-16 % faster than radix-16 stages (one stage and one
 // exchange fewer), else 4 (at 2^12 the radix-16 tiles keep three CTAs per SM and win);
@@ -193,6 +198,110 @@ void four_step_params(const fftc_plan_s *p, int logm, PassParams &a, PassParams 
     b.out_elem = M;
     b.post_line_mul = 1;
     b.post_elem_mul = M;
+}
+
+// FP64 table w_N^m for m < count, m scaled by `step` (m * step taken mod N), rounded once
+static fftc_status upload_roots(fftc_plan_s *p, int64_t N, int64_t count, int64_t step, float2 **out) {
+    std::vector<float2> t((size_t)count);
+    for (int64_t m = 0; m < count; ++m) {
+        double c, s;
+        unit_root((m * step) % N, N, &c, &s);
+        t[(size_t)m] = make_float2((float)c, (float)-s);
+    }
+    void *d = nullptr;
+    if (plan_upload(p, t.data(), t.size() * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    *out = (float2 *)d;
+    return FFTC_OK;
+}
+
+// Three HBM passes: Eq. 1 at the memory level twice, n = M K with K = P Q.
+//   pass 1 (columns): column j2 < K of every transform, M points at stride K, times
+//           w_n^(j2 k1), into ws1[b][k1][j2];
+//   pass 2 (columns, launched once per transform b): inside each row k1 of ws1, column
+//           j4 < Q, P points at stride Q, times w_K^(j4 k3), into ws2[b][k3][k1][j4];
+//   pass 3 (rows stored transposed): row (k3, k1) of ws2, Q points, output k4 to
+//           X[b n + k1 + M k3 + M P k4].
+// Every factor is at most 2^8, so every tile covers whole 128-byte rows; the price is a
+// third HBM round trip, which the narrow column bands of the two-pass form cost anyway.
+static fftc_status three_pass_build(fftc_plan_s *p, int lay) {
+    const int logm = 8, logk = p->logn - logm, logp = logk / 2, logq = logk - logp;
+    const int64_t n = p->n, B = p->batch, M = int64_t(1) << logm, K = n >> logm;
+    const int64_t P = int64_t(1) << logp, Q = int64_t(1) << logq;
+    const int64_t plane = lay == LAYOUT_SPLIT ? n * B : 0;
+    void *d = nullptr;
+    if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->workspace = (float2 *)d;
+    if (plan_alloc(p, (size_t)(n * B) * sizeof(float2), &d) != cudaSuccess) return FFTC_ERR_ALLOC;
+    p->workspace2 = (float2 *)d;
+    // w_n^m = lo[m mod 2^b] hi[m >> b] for pass 1, and the same for w_K in pass 2
+    fftc_status s;
+    p->tw2_lo_bits = (p->logn + 1) / 2;
+    if ((s = upload_roots(p, n, int64_t(1) << p->tw2_lo_bits, 1, &p->tw2_lo)) != FFTC_OK) return s;
+    if ((s = upload_roots(p, n, n >> p->tw2_lo_bits, int64_t(1) << p->tw2_lo_bits, &p->tw2_hi)) != FFTC_OK) return s;
+    const int kbits = (logk + 1) / 2;
+    float2 *klo = nullptr, *khi = nullptr;
+    if ((s = upload_roots(p, K, int64_t(1) << kbits, 1, &klo)) != FFTC_OK) return s;
+    if ((s = upload_roots(p, K, K >> kbits, int64_t(1) << kbits, &khi)) != FFTC_OK) return s;
+    p->npasses = 3;
+    p->three = true;
+    const int shape[3][5] = {{KIND_COLS, logm, lay, LAYOUT_IL, 1},
+                             {KIND_COLS, logp, LAYOUT_IL, LAYOUT_IL, 1},
+                             {KIND_ROWST, logq, LAYOUT_IL, lay, 0}};
+    for (int i = 0; i < 3; ++i) {
+        PassPlan &pp = p->pass[i];
+        pp.kind = shape[i][0];
+        pp.logl = shape[i][1];
+        pp.loge = 4;
+        pp.lines = 16;
+        pp.lin = shape[i][2];
+        pp.lout = shape[i][3];
+        pp.k = find_kernel(pp.kind, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, 0, 0);  // run-time strides
+        PassParams &b = pp.base;
+        memset(&b, 0, sizeof(b));
+        b.err = p->d_err;
+        set_wait_hooks(b);
+        b.pf_tiles = shape[i][4] ? -1 : 0;
+    }
+    PassParams &a = p->pass[0].base;
+    a.in_plane = plane;
+    a.total_lines = B * K;
+    a.log_lpt = logk;
+    a.in_tr = a.out_tr = n;
+    a.in_line = a.out_line = 1;
+    a.in_elem = a.out_elem = K;
+    a.tw2_lo = p->tw2_lo;
+    a.tw2_hi = p->tw2_hi;
+    a.log_n2 = p->logn;
+    a.tw2_lo_bits = p->tw2_lo_bits;
+    PassParams &c = p->pass[1].base;  // one transform b: lines (k1, j4)
+    c.total_lines = M * Q;
+    c.log_lpt = logq;
+    c.in_tr = K;
+    c.in_line = 1;
+    c.in_elem = Q;
+    c.out_tr = Q;
+    c.out_line = 1;
+    c.out_elem = M * Q;
+    c.tw2_lo = klo;
+    c.tw2_hi = khi;
+    c.log_n2 = logk;
+    c.tw2_lo_bits = kbits;
+    PassParams &r = p->pass[2].base;  // rows (b; k3 M + k1)
+    r.out_plane = plane;
+    r.total_lines = B * P * M;
+    r.log_lpt = logp + logm;
+    r.in_tr = r.out_tr = n;
+    r.in_line = Q;
+    r.in_elem = 1;
+    r.out_line = 1;
+    r.out_elem = M * P;
+    r.post_line_mul = 1;
+    r.post_elem_mul = M * P;
+    for (int i = 0; i < 3; ++i) {
+        if ((s = upload_stage_tables(p, p->pass[i])) != FFTC_OK) return s;
+        if ((s = prepare(p->pass[i])) != FFTC_OK) return s;
+    }
+    return FFTC_OK;
 }
 
 // Default cluster single pass per size (measured): clusters of R CTAs of Q = n / R points.
@@ -333,6 +442,13 @@ fftc_status plan_build_passes(fftc_plan_s *p) {
         if (ce) return cluster_setup(p, ce);
     }
 
+    // three HBM passes for the largest lengths (FFTC_THREE_PASS: 0 off, 1 from 2^21)
+    {
+        const int three = env_int("FFTC_THREE_PASS", -1);
+        if (!tc && p->logn >= 21 && (three == 1 || (three < 0 && p->logn >= kThreePassMinLog)))
+            return three_pass_build(p, lay);
+    }
+
     // four-step: n = M * K
     int logm, e1, e2, c1 = kPassLines, c2 = kPassLines, p1code = 0, p2code = 0, pf = 0;
     if (tc) {  // the FP32 shapes of 2^15 and 2^16 with 16 elements per thread, bulk-copy fed
@@ -434,6 +550,9 @@ fftc_status plan_build(fftc_plan_s *p) {
     return plan_build_passes(p);
 }
 
+static fftc_status three_pass_run(fftc_plan_s *p, const void *in, void *out, int64_t b0, int64_t nb,
+                                  const float *post_h, float post_scale, cudaStream_t st, cudaEvent_t *ev);
+
 fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *post_h, float post_scale,
                      cudaStream_t st) {
     cudaEvent_t *ev = nullptr;
@@ -486,6 +605,11 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
         if (ev) cudaEventRecord(ev[1], st);
         return FFTC_OK;
     }
+    if (p->three) {
+        fftc_status s = three_pass_run(p, in, out, 0, p->batch, post_h, post_scale, st, ev);
+        if (s == FFTC_OK && ev) cudaEventRecord(ev[2], st);
+        return s;
+    }
     PassParams a = p->pass[0].base;
     a.in = (const float *)in;
     a.out = (float *)p->workspace;
@@ -505,10 +629,40 @@ fftc_status plan_run(fftc_plan_s *p, const void *in, void *out, const float *pos
     return FFTC_OK;
 }
 
+// the three passes on transforms [b0, b0 + nb) (ev[1], when given, after pass 1)
+static fftc_status three_pass_run(fftc_plan_s *p, const void *in, void *out, int64_t b0, int64_t nb,
+                                  const float *post_h, float post_scale, cudaStream_t st, cudaEvent_t *ev) {
+    const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
+    const int64_t n = p->n, el = b0 * n;
+    const int64_t fo = p->layout == FFTC_LAYOUT_SPLIT ? el : 2 * el;  // float offset in the user layout
+    PassParams a = p->pass[0].base;
+    a.total_lines = a.total_lines / p->batch * nb;
+    a.in = (const float *)in + fo;
+    a.out = (float *)p->workspace + 2 * el;
+    a.conj_in = inv;
+    if (p->pass[0].k->launch(a, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    if (ev) cudaEventRecord(ev[1], st);
+    for (int64_t b = b0; b < b0 + nb; ++b) {
+        PassParams c = p->pass[1].base;
+        c.in = (const float *)p->workspace + 2 * b * n;
+        c.out = (float *)p->workspace2 + 2 * b * n;
+        if (p->pass[1].k->launch(c, st) != cudaSuccess) return FFTC_ERR_CUDA;
+    }
+    PassParams r = p->pass[2].base;
+    r.total_lines = r.total_lines / p->batch * nb;
+    r.in = (const float *)p->workspace2 + 2 * el;
+    r.out = (float *)out + fo;
+    r.conj_out = inv;
+    r.post_h = post_h;
+    r.post_scale = post_scale;
+    return p->pass[2].k->launch(r, st) == cudaSuccess ? FFTC_OK : FFTC_ERR_CUDA;
+}
+
 fftc_status plan_run_range(fftc_plan_s *p, const void *in, void *out, int64_t b0, int64_t nb, cudaStream_t st) {
     if (p->uneven || p->fs || p->mixed || p->nd || p->precision != FFTC_FP32 || b0 < 0 || nb < 0 || b0 + nb > p->batch)
         return FFTC_ERR_INVALID_VALUE;
     if (nb == 0) return FFTC_OK;
+    if (p->three) return three_pass_run(p, in, out, b0, nb, nullptr, 0.f, st, nullptr);
     const int inv = p->direction == FFTC_INVERSE ? 1 : 0;
     // complex offset of transform b0: interleaved buffers count floats in pairs, the split
     // planes count one float per element (the plane stride stays the whole batch's)

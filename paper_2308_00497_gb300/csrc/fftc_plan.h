@@ -39,8 +39,12 @@ struct fftc_plan_s {
     fftc_direction direction = FFTC_FORWARD;
     fftc_precision precision = FFTC_FP32;
     int npasses = 0;
-    fftc::PassPlan pass[2] = {};
+    fftc::PassPlan pass[3] = {};
     float2 *workspace = nullptr;
+    // three HBM passes (n = M P Q, Eq. 1 twice at the memory level): pass[1] runs once per
+    // transform of the batch and writes workspace2
+    bool three = false;
+    float2 *workspace2 = nullptr;
     float2 *tw2_lo = nullptr, *tw2_hi = nullptr, *tw2_full = nullptr;
     int tw2_lo_bits = 0;
     int *d_err = nullptr;  // device error word (bounded waits)

@@ -354,7 +354,7 @@ fftc_status plan_tune(fftc_plan_s *p, int reps) {
     if (p->batch == 0) return FFTC_OK;
     if (p->mixed) return mixed_tune(p, reps);
     if (p->nd) return nd_tune(p, reps);
-    if (p->uneven || p->fs) return FFTC_OK;
+    if (p->uneven || p->fs || p->three) return FFTC_OK;
     if (reps < 1) reps = 1;
     const int lay = p->layout == FFTC_LAYOUT_SPLIT ? LAYOUT_SPLIT : LAYOUT_IL;
     const auto key = std::make_tuple(p->n, p->batch, (int)p->layout, (int)p->direction, (int)p->precision);

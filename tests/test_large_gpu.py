@@ -1,8 +1,9 @@
 """Lengths above 2^20, up to 2^24.
 
 FP32 powers of two run Eq. 1 once at the memory level with a factor of 2^11 or 2^12
-(column tiles of 8 or 4 lines, transposed-row tiles of 8 or 4 lines); FP32 mixed lengths
-and FP64 run the runtime-radix path, whose split can hold lines longer than 4096.
+(column tiles of 8 or 4 lines, transposed-row tiles of 8 or 4 lines), or twice (three HBM
+passes, n = 2^8 P Q with P, Q <= 2^8); FP32 mixed lengths and FP64 run the runtime-radix
+path, whose split can hold lines longer than 4096.
 
 Powers of two: element-wise parity with the FP64 oracle (radix-2: seconds at 2^24) at
 every size, both layouts and directions, one to three transforms, and sampled rows of
@@ -56,7 +57,7 @@ def test_parity_powers_of_two_above_2p20(e, inverse, layout):
     n = 1 << e
     x = _input(e)
     p = fc.Plan(n, x.shape[0], layout, inverse)
-    assert p.info()[0] == 2
+    assert p.info()[0] in (2, 3)
     y = from_device(p.execute(to_device(x, layout)), layout)
     torch.cuda.synchronize()
     p.check()
@@ -212,3 +213,50 @@ def test_fp64_mixed_above_2p20_tone(n):
     want = np.zeros((1, n), np.complex128)
     want[0, k0] = n
     assert rel_l2_rows(y, want).max() <= 1e-14 * math.log2(n)
+
+
+@pytest.mark.parametrize("e", [21, 22, 23, 24])
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+@pytest.mark.parametrize("three", ["0", "1"])
+def test_two_and_three_pass_forms(monkeypatch, e, inverse, layout, three):
+    """Eq. 1 once at the memory level (two HBM passes) and twice (three passes: columns of
+    2^8 at stride n / 2^8, then per transform columns of P at stride Q inside each row, then
+    rows of Q stored transposed), each forced, element-wise against the oracle."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_THREE_PASS", three)
+    n = 1 << e
+    x = _input(e)
+    p = fc.Plan(n, x.shape[0], layout, inverse)
+    assert p.info()[0] == (3 if three == "1" else 2)
+    if three == "1":
+        assert p.split() == (256, n // 256)
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    err = rel_l2_rows(y, _reference(e, inverse))
+    assert err.max() <= tol_fp32(n), (n, layout, inverse, three, float(err.max()))
+
+
+def test_three_pass_pointwise_and_host_chunks(monkeypatch):
+    """Three-pass plan at 2^22 x 6: the fused pointwise multiply of the last pass (frequency
+    k1 + M k3 + M P k4) against the oracle times H, and host-buffer execution in chunks
+    bitwise equal to the device path."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_THREE_PASS", "1")
+    n, B = 1 << 22, 6
+    x = si.uniform_complex(B, n, seed=2323)
+    p = fc.Plan(n, B, "interleaved", False)
+    assert p.info()[0] == 3
+    xd = to_device(x, "interleaved")
+    h = torch.from_numpy(si.gaussian_lowpass(n)).cuda()
+    yp = p.execute_pointwise(xd, h, 0.5)
+    dev = p.execute(xd)
+    torch.cuda.synchronize()
+    ref = oracle.fft(x[[0, B - 1]].astype(np.complex128)) * (0.5 * h.cpu().numpy().astype(np.float64))
+    assert rel_l2_rows(yp.cpu().numpy()[[0, B - 1]], ref).max() <= tol_fp32(n)
+    xs = xd.cpu().pin_memory()
+    out = torch.empty_like(xs).pin_memory()
+    buf = torch.empty_like(xs, device="cuda")
+    p.execute_host(xs, out, buf)
+    assert torch.equal(out.view(torch.int32), dev.cpu().view(torch.int32))
