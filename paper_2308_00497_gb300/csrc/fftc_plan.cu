@@ -260,7 +260,7 @@ static fftc_status three_pass_build(fftc_plan_s *p, int lay) {
         memset(&b, 0, sizeof(b));
         b.err = p->d_err;
         set_wait_hooks(b);
-        b.pf_tiles = shape[i][4] ? -1 : 0;
+        b.pf_tiles = (shape[i][4] && env_int("FFTC_PF", 1)) ? -1 : 0;
     }
     PassParams &a = p->pass[0].base;
     a.in_plane = plane;
