@@ -256,8 +256,9 @@ fftc_status fftc_plan_timing(fftc_plan plan, int enable);
 
 /*
  * Per-pass device time of the executes recorded since the probe was enabled:
- * ms_per_pass[i] = summed elapsed milliseconds of pass i (i < 2), *executes = how many
- * executes were recorded. Synchronises on the recorded events.
+ * ms_per_pass[i] = summed elapsed milliseconds of pass i (i < 2; for a three-pass plan
+ * ms_per_pass[1] holds passes 2 and 3 together), *executes = how many executes were
+ * recorded. Synchronises on the recorded events.
  */
 fftc_status fftc_plan_pass_times(fftc_plan plan, double *ms_per_pass, int *executes);
 
