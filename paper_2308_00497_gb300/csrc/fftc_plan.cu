@@ -244,18 +244,25 @@ static fftc_status three_pass_build(fftc_plan_s *p, int lay) {
     if ((s = upload_roots(p, K, K >> kbits, int64_t(1) << kbits, &khi)) != FFTC_OK) return s;
     p->npasses = 3;
     p->three = true;
-    const int shape[3][5] = {{KIND_COLS, logm, lay, LAYOUT_IL, 1},
-                             {KIND_COLS, logp, LAYOUT_IL, LAYOUT_IL, 1},
-                             {KIND_ROWST, logq, LAYOUT_IL, lay, 0}};
+    // kind, line length, layouts, L2 prefetch, element stride compiled into the kernel when
+    // one is (pass 1: in and out K; pass 3: out M P; pass 2's two strides differ)
+    const int shape[3][6] = {{KIND_COLS, logm, lay, LAYOUT_IL, 1, logk},
+                             {KIND_COLS, logp, LAYOUT_IL, LAYOUT_IL, 1, 0},
+                             {KIND_ROWST, logq, LAYOUT_IL, lay, 0, logm + logp}};
+    const int c1 = env_int("FFTC_TUNE_COLS_C", 16);
     for (int i = 0; i < 3; ++i) {
         PassPlan &pp = p->pass[i];
         pp.kind = shape[i][0];
         pp.logl = shape[i][1];
         pp.loge = 4;
-        pp.lines = 16;
+        pp.lines = i == 0 ? c1 : 16;
         pp.lin = shape[i][2];
         pp.lout = shape[i][3];
-        pp.k = find_kernel(pp.kind, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, 0, 0);  // run-time strides
+        pp.k = find_kernel(pp.kind, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, 0, shape[i][5]);
+        if (!pp.k) {  // run-time strides, 16 lines a tile
+            pp.lines = 16;
+            pp.k = find_kernel(pp.kind, pp.logl, pp.loge, pp.lines, pp.lin, pp.lout, 0, 0);
+        }
         PassParams &b = pp.base;
         memset(&b, 0, sizeof(b));
         b.err = p->d_err;

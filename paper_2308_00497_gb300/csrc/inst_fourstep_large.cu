@@ -14,9 +14,17 @@ namespace fftc {
 #define LT(LOGL, LOGE, C) entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_IL, 0>(), \
                           entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT, 0>()
 
+// three-pass 2^24 (n = 2^8 x 2^8 x 2^8): pass 1 columns of 256 at the element stride 2^16
+// (16 or 32 columns a tile) and pass 3 rows of 256 stored at the stride 2^16, at compile time
+#define LCX(LOGL, LOGE, C, LOGX) entry<LOGL, LOGE, C, KIND_COLS, LAYOUT_IL, LAYOUT_IL, LOGX>(), \
+                                 entry<LOGL, LOGE, C, KIND_COLS, LAYOUT_SPLIT, LAYOUT_IL, LOGX>()
+#define LTX(LOGL, LOGE, C, LOGX) entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_IL, LOGX>(), \
+                                 entry<LOGL, LOGE, C, KIND_ROWST, LAYOUT_IL, LAYOUT_SPLIT, LOGX>()
+
 extern const KernelEntry kLargeTable[] = {
     LC(11, 5, 8), LC(12, 5, 4), LC(11, 4, 8), LC(11, 5, 4), LC(12, 4, 4),
     LT(11, 5, 8), LT(12, 5, 4), LT(11, 4, 8), LT(11, 5, 4), LT(12, 4, 4),
+    LCX(8, 4, 16, 16), LCX(8, 4, 32, 16), LTX(8, 4, 16, 16),
 };
 extern const int kLargeCount = sizeof(kLargeTable) / sizeof(kLargeTable[0]);
 

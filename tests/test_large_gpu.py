@@ -260,3 +260,20 @@ def test_three_pass_pointwise_and_host_chunks(monkeypatch):
     buf = torch.empty_like(xs, device="cuda")
     p.execute_host(xs, out, buf)
     assert torch.equal(out.view(torch.int32), dev.cpu().view(torch.int32))
+
+
+@pytest.mark.parametrize("layout", ["interleaved", "split"])
+def test_three_pass_32_column_bands_2p24(monkeypatch, layout):
+    """Three-pass 2^24 with 32-column tiles in pass 1 (256-byte rows, the element stride
+    2^16 compiled into the kernel), element-wise against the oracle."""
+    import paper_2308_00497_gb300 as fc
+    monkeypatch.setenv("FFTC_THREE_PASS", "1")
+    monkeypatch.setenv("FFTC_TUNE_COLS_C", "32")
+    e = 24
+    x = _input(e)
+    p = fc.Plan(1 << e, x.shape[0], layout, False)
+    assert p.info()[0] == 3
+    y = from_device(p.execute(to_device(x, layout)), layout)
+    torch.cuda.synchronize()
+    p.check()
+    assert rel_l2_rows(y, _reference(e, False)).max() <= tol_fp32(1 << e)
