@@ -249,7 +249,9 @@ static fftc_status three_pass_build(fftc_plan_s *p, int lay) {
     const int shape[3][6] = {{KIND_COLS, logm, lay, LAYOUT_IL, 1, logk},
                              {KIND_COLS, logp, LAYOUT_IL, LAYOUT_IL, 1, 0},
                              {KIND_ROWST, logq, LAYOUT_IL, lay, 0, logm + logp}};
-    const int c1 = env_int("FFTC_TUNE_COLS_C", 16);
+    // pass 1 in 32-column tiles (256-byte rows) where compiled: at 2^24 the split layout's
+    // pass 1 measured 0.301 -> 0.267 ms against 16 columns (interleaved even)
+    const int c1 = env_int("FFTC_TUNE_COLS_C", 32);
     for (int i = 0; i < 3; ++i) {
         PassPlan &pp = p->pass[i];
         pp.kind = shape[i][0];

@@ -263,12 +263,12 @@ def test_three_pass_pointwise_and_host_chunks(monkeypatch):
 
 
 @pytest.mark.parametrize("layout", ["interleaved", "split"])
-def test_three_pass_32_column_bands_2p24(monkeypatch, layout):
-    """Three-pass 2^24 with 32-column tiles in pass 1 (256-byte rows, the element stride
-    2^16 compiled into the kernel), element-wise against the oracle."""
+def test_three_pass_16_column_bands_2p24(monkeypatch, layout):
+    """Three-pass 2^24 with 16-column tiles in pass 1 (the default has 32; the element
+    stride 2^16 compiled into the kernel), element-wise against the oracle."""
     import paper_2308_00497_gb300 as fc
     monkeypatch.setenv("FFTC_THREE_PASS", "1")
-    monkeypatch.setenv("FFTC_TUNE_COLS_C", "32")
+    monkeypatch.setenv("FFTC_TUNE_COLS_C", "16")
     e = 24
     x = _input(e)
     p = fc.Plan(1 << e, x.shape[0], layout, False)
